@@ -1,0 +1,363 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: a
+closed form, an identity the paper derives, an exhaustive enumeration, a
+library routine in a special case or a brute-force sum.  No GPU needed.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import epic_synth as synth
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# unpack (4-bit complex input format)
+# --------------------------------------------------------------------------
+def test_unpack_exhaustive_roundtrip():
+    """All 256 bytes: unpack is the inverse of the generator's packing, a
+    bijection onto [-8, 7]^2."""
+    re, im = np.meshgrid(np.arange(-8, 8), np.arange(-8, 8), indexing="ij")
+    b = synth.pack_ci4(re.ravel(), im.ravel())
+    assert sorted(b.tolist()) == list(range(256))
+    z = O.unpack_ci4(b)
+    assert np.array_equal(z.real, re.ravel()) and np.array_equal(z.imag, im.ravel())
+
+
+def test_unpack_golden_bytes():
+    """Hand-decoded bytes (two's complement nibbles)."""
+    with open(os.path.join(GOLDEN, "ci4_bytes.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        z = O.unpack_ci4(np.array([c["byte"]], np.uint8))[0]
+        assert (z.real, z.imag) == (c["re"], c["im"]), c
+
+
+# --------------------------------------------------------------------------
+# grid table (Eq. 9 stencil and kernel)
+# --------------------------------------------------------------------------
+def test_grid_table_cell_centre_special_case():
+    """An antenna exactly on a cell centre: base = that cell, and the 3x3
+    Gaussian weights are the normalised products of 1 and e^{-1/(2 s^2)}."""
+    f = 50e6
+    lam = O.C_LIGHT / f
+    N, du = 16, 0.5
+    # x = 3 cells east, y = 2 cells south of the centre
+    ant = np.array([[3 * du * lam, -2 * du * lam]])
+    base, W = O.grid_table(ant, [f], N, du, "gaussian", 3, 0.5)
+    assert tuple(base[0, 0]) == (N // 2 + 3, N // 2 - 2)
+    e = np.exp(-1.0 / (2 * 0.25))
+    w1 = np.array([e, 1.0, e])
+    expect = np.outer(w1, w1) / np.outer(w1, w1).sum()
+    assert np.allclose(W[0, 0], expect, rtol=0, atol=1e-12)
+
+
+def test_grid_table_properties_random():
+    rng = np.random.default_rng(3)
+    ant = rng.uniform(-10, 10, size=(40, 2))
+    freqs = [40e6, 63e6, 80e6]
+    N, du = 64, 0.5
+    base, W = O.grid_table(ant, freqs, N, du, "gaussian", 5, 0.7)
+    for c, f in enumerate(freqs):
+        p = ant * f / O.C_LIGHT / du + N / 2
+        # nearest cell
+        assert np.all(np.abs(base[c] - p) <= 0.5)
+        # normalised: far-field pattern is 1 at the centre
+        assert np.allclose(W[c].sum(axis=(1, 2)), 1.0, atol=1e-14)
+        # largest tap is the centre tap (nearest cell)
+        assert np.all(W[c].reshape(len(ant), -1).argmax(axis=1) == 12)
+    # mirroring the array in x mirrors the weights in dx
+    base2, W2 = O.grid_table(ant * np.array([-1, 1]), freqs, N, du, "gaussian", 5, 0.7)
+    for c, f in enumerate(freqs):
+        # away from exact half-cell ties, where the nearest cell flips side
+        ok = np.abs((ant[:, 0] * f / O.C_LIGHT / du) % 1 - 0.5) > 1e-9
+        assert np.allclose(W2[c, ok], W[c, ok][..., ::-1], atol=1e-13)
+
+
+def test_grid_table_tophat_counts():
+    """Tophat of side s metres covers the cells whose centres lie within
+    s/2 of the antenna on both axes; weights are 1/count."""
+    f = 60e6
+    lam = O.C_LIGHT / f
+    du = 0.5
+    ant = np.array([[0.0, 0.0], [0.3 * du * lam, 0.05 * du * lam]])
+    # side 2.2 cells: half 1.1 cells -> 3 x 3 cells around a centred antenna
+    base, W = O.grid_table(ant, [f], 32, du, "tophat", 5, 2.2 * du * lam)
+    assert np.count_nonzero(W[0, 0]) == 9 and np.allclose(W[0, 0][W[0, 0] > 0], 1 / 9)
+    # offset antenna: x in [-0.8, 1.4] cells -> cells 0, 1; y in [-1.05, 1.15] -> -1, 0, 1
+    assert np.count_nonzero(W[0, 1]) == 6 and np.allclose(W[0, 1][W[0, 1] > 0], 1 / 6)
+
+
+def test_grid_table_overflow():
+    f = 80e6
+    lam = O.C_LIGHT / f
+    ant = np.array([[7.6 * 0.5 * lam, 0.0]])  # cell 16+8 = 23.6 -> 24 -> taps 23..25
+    with pytest.raises(O.GridTooSmall):
+        O.grid_table(ant, [f], 16, 0.5)
+    # flagged antennas are not checked
+    O.grid_table(ant, [f], 16, 0.5, flags=[1])
+
+
+# --------------------------------------------------------------------------
+# E-field image (Eq. 10)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_dft_separable_equals_direct(n):
+    rng = np.random.default_rng(n)
+    G = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    a = O.efield_image(G, 7)
+    b = O.efield_image_direct(G, 7)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("n", [8, 32, 128])
+def test_dft_equals_numpy_ifft(n):
+    """Library special case: with sign flips (-1)^(jx+jy) on the grid and
+    (-1)^(kx+ky) on the image, Eq. 10 is N^2 ifft2 / Na."""
+    rng = np.random.default_rng(n + 1)
+    G = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    s = (-1.0) ** np.add.outer(np.arange(n), np.arange(n))
+    ref = s * np.fft.ifft2(s * G) * n * n / 5.0
+    got = O.efield_image(G, 5)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_dft_single_cell_phase_ramp():
+    """One non-zero cell gives a pure phase ramp of unit modulus / Na."""
+    n = 16
+    G = np.zeros((n, n), complex)
+    jx, jy = 11, 3
+    G[jy, jx] = 1.0
+    img = O.efield_image(G, 4)
+    assert np.allclose(np.abs(img), 0.25, atol=1e-14)
+    # phase at (kx, ky) = (N/2 + 1, N/2): 2 pi (jx - N/2) / N
+    assert np.isclose(np.angle(img[n // 2, n // 2 + 1]),
+                      np.angle(np.exp(2j * np.pi * (jx - n // 2) / n)), atol=1e-12)
+    assert np.isclose(img[n // 2, n // 2], 0.25, atol=1e-15)
+
+
+def test_point_source_images_at_its_direction():
+    """Sign convention: a noise-free point source at pixel (kx, ky) gives the
+    brightest dirty-image pixel there (Eq. 3 propagation, Eq. 10 imaging)."""
+    rng = np.random.default_rng(5)
+    N, du, f = 32, 0.5, 50e6
+    ant = synth.layout_disc(24, 20.0, rng, 1.0)
+    kx, ky = 21, 12
+    l, m = (kx - N / 2) / (N * du), (ky - N / 2) / (N * du)
+    sky = np.array([[l, m, 1.0]])
+    E = synth.voltages(ant, [f], np.ones((1, 24)), sky, 64, 0.0, rng)
+    plan = O.Plan(ant, [f], N, du)
+    img, _ = O.image_interval(plan, E, np.ones((1, 24)))
+    assert np.unravel_index(np.argmax(img[0]), img[0].shape) == (ky, kx)
+    assert O.calibrator_pixel(l, m, N, du) == (kx, ky)
+
+
+def _explicit_A(plan, c):
+    """A_{k,a} for every pixel k by explicit sums over taps (test-local)."""
+    N = plan.N
+    Na = plan.Na
+    K = plan.W.shape[-1]
+    h = (K - 1) // 2
+    A = np.zeros((N, N, Na), complex)
+    ky, kx = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    for a in range(Na):
+        if plan.flags[a]:
+            continue
+        for dy in range(K):
+            for dx in range(K):
+                jx = plan.base[c, a, 0] + dx - h
+                jy = plan.base[c, a, 1] + dy - h
+                ph = 2 * np.pi * ((jx - N // 2) * (kx - N // 2) + (jy - N // 2) * (ky - N // 2)) / N
+                A[:, :, a] += plan.W[c, a, dy, dx] * np.exp(1j * ph)
+    return A / plan.norm
+
+
+def test_image_equals_gridded_visibilities_with_autos():
+    """Sec. 2.1: the squared, averaged E-field image equals the image made
+    from all antenna-pair visibilities, autos included:
+    I_k = sum_{a,b} A_{k,a} conj(A_{k,b}) V'_ab, V'_ab = <E'_a conj(E'_b)>."""
+    rng = np.random.default_rng(11)
+    Na, N, T = 6, 16, 48
+    ant = synth.layout_disc(Na, 8.0, rng, 1.0)
+    f = [45e6, 70e6]
+    g = synth.true_gains(2, Na, rng)
+    sky = np.array([[0.0, 0.0, 3.0], [0.3, -0.2, 1.0]])
+    E = synth.voltages(ant, f, g, sky, T, 1.0, rng)
+    flags = np.zeros(Na, bool)
+    flags[4] = True
+    plan = O.Plan(ant, f, N, 0.5, flags=flags)
+    gcur = synth.true_gains(2, Na, rng)
+    img, _ = O.image_interval(plan, E, gcur, block=17)
+    for c in range(2):
+        A = _explicit_A(plan, c)
+        Ec = E[:, c, :] / gcur[c]
+        V = Ec.T @ np.conj(Ec) / T
+        ref = np.einsum("yxa,ab,yxb->yx", A, V, np.conj(A)).real
+        assert np.max(np.abs(img[c] - ref)) <= 1e-12 * np.max(ref)
+
+
+# --------------------------------------------------------------------------
+# EPICal (Eqs. 12-17)
+# --------------------------------------------------------------------------
+def _tiny_plan_and_data(rng, Na=8, N=16, T=200, cal=(0.0, 0.0), noise=0.5, unit=False,
+                        sky=None, flags=None):
+    ant = synth.layout_disc(Na, 8.0, rng, 1.0)
+    f = [50e6]
+    g = synth.true_gains(1, Na, rng)
+    if sky is None:
+        sky = np.array([[cal[0], cal[1], 4.0], [0.25, 0.1, 1.0]])
+    E = synth.voltages(ant, f, g, sky, T, noise, rng, unit_modulus=unit)
+    plan = O.Plan(ant, f, N, 0.5, cal_lm=cal, model_lmS=sky, flags=flags)
+    return plan, E, g
+
+
+def test_correlation_equals_visibility_route():
+    """Eqs. 13 -> 15 are exact sample-average algebra: C_a from the image
+    pixel equals sum_{b != a} conj(A_{0,b}) V_ab / conj(g_b)."""
+    rng = np.random.default_rng(2)
+    k0 = (19, 13)
+    cal = ((k0[0] - 16) / 16.0, (k0[1] - 16) / 16.0)
+    flags = np.zeros(9, bool)
+    flags[2] = True
+    plan, E, g = _tiny_plan_and_data(rng, Na=9, N=32, cal=cal, flags=flags)
+    gcur = synth.true_gains(1, 9, rng)[0]
+    _, pix = O.image_interval(plan, E, gcur[None])
+    Kc, P = O.correlate(E[:, 0, :], pix[:, 0])
+    Cc = Kc - np.conj(plan.A0[0]) * P / np.conj(gcur)
+    V = O.visibilities(E[:, 0, :])
+    ref = np.array([sum(np.conj(plan.A0[0, b]) * V[a, b] / np.conj(gcur[b])
+                        for b in range(9) if b != a and not flags[b]) for a in range(9)])
+    assert np.max(np.abs(Cc - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_zenith_single_source_limit():
+    """Eqs. 18-19: for s0 at the phase centre A_{0,b} = 1/Na exactly, and
+    Na C_a = sum_{b != a} V_ab / conj(g_b); the undamped update is that sum
+    over (Na - 1) S (Eq. 16 literally; Eq. 19's Na S is its large-Na form)."""
+    rng = np.random.default_rng(4)
+    Na = 10
+    sky = np.array([[0.0, 0.0, 2.5]])
+    plan, E, g = _tiny_plan_and_data(rng, Na=Na, sky=sky)
+    assert np.allclose(plan.A0[0], 1.0 / Na, atol=1e-15)
+    gcur = synth.true_gains(1, Na, rng)[0]
+    _, pix = O.image_interval(plan, E, gcur[None])
+    Kc, P = O.correlate(E[:, 0, :], pix[:, 0])
+    V = O.visibilities(E[:, 0, :])
+    Cc = Kc - np.conj(plan.A0[0]) * P / np.conj(gcur)
+    ref = np.array([sum(V[a, b] / np.conj(gcur[b]) for b in range(Na) if b != a)
+                    for a in range(Na)])
+    assert np.allclose(Na * Cc, ref, rtol=1e-12, atol=0)
+    gn, _ = O.epical_update(Kc, P, plan.A0[0], plan.D[0], gcur, 0.0)
+    assert np.allclose(gn, ref / ((Na - 1) * 2.5), rtol=1e-12)
+
+
+@pytest.mark.parametrize("cal", [(0.0, 0.0), (0.25, -0.125)])
+def test_noise_free_converges_to_true_gains(cal):
+    """One unit-modulus source at the calibrator pixel, no noise, injected
+    gains: EPICal from g = 1 converges to g e^{i phi}."""
+    rng = np.random.default_rng(7)
+    Na = 12
+    sky = np.array([[cal[0], cal[1], 3.0]])
+    plan, E, g = _tiny_plan_and_data(rng, Na=Na, N=16, T=32, sky=sky, noise=0.0,
+                                     unit=True)
+    gcur = np.ones((1, Na), complex)
+    for _ in range(80):
+        gcur, *_ = O.epical_interval(plan, E, gcur, 0.35, with_image=False)
+    ga = O.align_phase(gcur[0], g[0])
+    assert np.max(np.abs(ga - g[0]) / np.abs(g[0])) < 1e-10
+
+
+def test_damping_closed_form_and_effective_time():
+    """Eq. 17 with a fixed C/D = x gives g^(n) = x + gamma^n (g0 - x); the
+    weights (1-gamma) gamma^k give t_eff / t_cal = (1+gamma)/(1-gamma)
+    (Eq. 20) for the variance of i.i.d. inputs."""
+    gamma = 0.35
+    A0 = np.array([0.0j, 0.0j])
+    D = np.array([2.0 + 1.0j, -1.0 + 0.5j])
+    Kc = np.array([1.0 - 2.0j, 0.5 + 0.25j])
+    P = np.zeros(2)
+    g0 = np.array([1.0 + 0j, 1.0 + 0j])
+    x = Kc / D
+    g = g0.copy()
+    for n in range(1, 30):
+        g, _ = O.epical_update(Kc, P, A0, D, g, gamma)
+        assert np.allclose(g, x + gamma ** n * (g0 - x), rtol=1e-13)
+    # impulse responses: weight of the input j steps back
+    n_steps = 200
+    w = []
+    for j in range(n_steps):
+        gg = np.ones(1, complex)   # start value decays as gamma^n_steps ~ 0
+        for n in range(n_steps):
+            k = np.array([1.0 + 0j]) if n == n_steps - 1 - j else np.zeros(1, complex)
+            gg, _ = O.epical_update(k, np.zeros(1), np.zeros(1, complex),
+                                    np.ones(1, complex), gg, gamma)
+        w.append(gg[0].real)
+    w = np.array(w)
+    assert np.isclose(w.sum(), 1.0, atol=1e-12)
+    assert np.isclose(1.0 / np.sum(w ** 2), (1 + gamma) / (1 - gamma), rtol=1e-10)
+
+
+def test_update_holds_flagged_and_bad_antennas():
+    A0 = np.full(4, 0.25 + 0j)
+    D = np.array([1.0 + 0j, 0.0 + 0j, 1.0 + 0j, 1.0 + 0j])
+    Kc = np.array([1.0 + 0j, 1.0 + 0j, np.nan + 0j, 1.0 + 0j])
+    g = np.array([2.0 + 0j, 3.0 + 0j, 4.0 + 0j, 5.0 + 0j])
+    gn, held = O.epical_update(Kc, np.zeros(4), A0, D, g, 0.5, flags=[0, 0, 0, 1])
+    assert held.tolist() == [False, True, True, True]
+    assert gn[1:].tolist() == g[1:].tolist()
+    with pytest.raises(ValueError):
+        O.epical_update(Kc, np.zeros(4), A0, D, g, 1.0)
+
+
+def test_epical_agrees_with_visibility_solve_noise_free():
+    """Sec. 4 comparison: on noise-free single-source data both the EPICal
+    loop and the Eq. 21 visibility solve recover the true gains up to a
+    global phase."""
+    rng = np.random.default_rng(8)
+    Na = 10
+    sky = np.array([[0.0, 0.0, 2.0]])
+    plan, E, g = _tiny_plan_and_data(rng, Na=Na, N=16, T=24, sky=sky, noise=0.0, unit=True)
+    V = O.visibilities(E[:, 0, :])
+    VM = O.model_visibilities(plan.ant, plan.freqs[0], sky)
+    gv = O.visibility_solve(V, VM, np.ones(Na, complex))
+    gcur = np.ones((1, Na), complex)
+    for _ in range(80):
+        gcur, *_ = O.epical_interval(plan, E, gcur, 0.35, with_image=False)
+    ge = O.align_phase(gcur[0], g[0])
+    gvv = O.align_phase(gv, g[0])
+    assert np.max(np.abs(ge - gvv) / np.abs(g[0])) < 1e-10
+    assert O.gain_error(gvv, g[0]) < 1e-10
+
+
+def test_visibility_solve_noisy_reduces_chi2():
+    rng = np.random.default_rng(9)
+    Na = 12
+    plan, E, g = _tiny_plan_and_data(rng, Na=Na, N=16, T=400, noise=1.0)
+    sky = np.array([[0.0, 0.0, 4.0], [0.25, 0.1, 1.0]])
+    V = O.visibilities(E[:, 0, :])
+    VM = O.model_visibilities(plan.ant, plan.freqs[0], sky)
+    off = ~np.eye(Na, dtype=bool)
+
+    def chi2(gg):
+        return np.sum(np.abs(V - np.outer(gg, np.conj(gg)) * VM)[off] ** 2)
+
+    gv = O.visibility_solve(V, VM, np.ones(Na, complex))
+    assert chi2(gv) < chi2(g[0]) * 1.0000001
+    # stationarity: small perturbations do not lower chi^2
+    for d in (1e-4, 1e-4j):
+        for a in range(3):
+            gp = gv.copy()
+            gp[a] += d
+            assert chi2(gp) >= chi2(gv) - 1e-12
+
+
+def test_gain_error_metric():
+    gt = np.array([[1 + 1j, 2.0 + 0j]])
+    ge = np.array([[1.1 + 1.1j, 2.0 + 0.2j]])
+    # |0.1(1+i)|^2/|1+i|^2 = 0.01 ; |0.2i|^2/4 = 0.01
+    assert np.isclose(O.gain_error(ge, gt), 0.1)
