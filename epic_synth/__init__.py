@@ -222,3 +222,37 @@ def workload(name: str, seed: int | None = None, n_time: int | None = None,
                     n_time=n_time or (10000 if name == "lwa" else 4096),
                     noise_power=noise, input="ci4", gamma=0.5, lsb=lsb, rng=rng)
     raise ValueError(name)
+
+
+def voltages_ci4_torch(ant_xy_m, freq_hz, gains, sky_lmS, n_time, noise_power, lsb,
+                       seed: int, device="cuda", chunk: int = 4096):
+    """Large-workload generator on a torch device: the same data model as
+    `voltages`, drawn with a seeded torch.Generator, quantised straight to
+    the 4-bit byte format.  Returns a uint8 tensor [T][C][Na] on `device`."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    ant = torch.as_tensor(np.asarray(ant_xy_m, np.float64), device=device)
+    sky = torch.as_tensor(np.asarray(sky_lmS, np.float64), device=device)
+    T, C, Na, Ns = int(n_time), len(freq_hz), ant.shape[0], sky.shape[0]
+    out = torch.empty((T, C, Na), dtype=torch.uint8, device=device)
+    amp = torch.sqrt(sky[:, 2]).to(torch.float32)
+    g = torch.as_tensor(np.asarray(gains), device=device).to(torch.complex64)
+    for c, f in enumerate(freq_hz):
+        u = ant * float(f) / C_LIGHT
+        ph = torch.exp(-2j * np.pi * (u @ sky[:, :2].T)).to(torch.complex64)   # [Na][Ns]
+        q = float(np.asarray(lsb).reshape(-1)[c]) if np.ndim(lsb) else float(lsb)
+        for t0 in range(0, T, chunk):
+            n = min(chunk, T - t0)
+            zr = torch.randn((n, Ns), generator=gen, device=device)
+            zi = torch.randn((n, Ns), generator=gen, device=device)
+            z = torch.complex(zr, zi) * (amp / np.sqrt(2.0))
+            e = (z @ ph.T) * g[c][None, :]
+            if noise_power > 0:
+                nr = torch.randn((n, Na), generator=gen, device=device)
+                ni = torch.randn((n, Na), generator=gen, device=device)
+                e = e + torch.complex(nr, ni) * float(np.sqrt(noise_power / 2))
+            re = torch.clamp(torch.round(e.real / q), -7, 7).to(torch.int32)
+            im = torch.clamp(torch.round(e.imag / q), -7, 7).to(torch.int32)
+            out[t0:t0 + n, c, :] = (((re & 15) << 4) | (im & 15)).to(torch.uint8)
+    return out

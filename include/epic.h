@@ -1,0 +1,186 @@
+/*
+ * epic.h - C ABI of the GB300 EPIC/EPICal library.
+ *
+ * EPIC (E-field Parallel Imaging Correlator) direct imaging and the EPICal
+ * feedback calibration of Beardsley et al., "An Efficient Feedback
+ * Calibration Algorithm for Direct Imaging Radio Telescopes".  Per time
+ * sample t and channel c (one "frame"):
+ *   E'_a = E_a / g_a                       gain correction          (Eq. 8)
+ *   E'_j = sum_a W_a(r_j - r_a) E'_a        gridding                 (Eq. 9)
+ *   E'(s_k) = (1/Na) sum_j e^{+2 pi i ...} E'_j   2D FFT             (Eq. 10)
+ *   I'(s_k) += |E'(s_k)|^2 / T             square and average (Sec. 2.1)
+ *   K_a += E_a conj(E'(s0)), P_a += |E_a|^2  EPICal correlation (Eqs. 12, 15)
+ * and per calibration interval the damped gain update (Eqs. 15-17).
+ *
+ * Conventions (all calls):
+ *  - Every call returns an epic_status; on failure epic_last_error() gives a
+ *    thread-local message.  No call aborts the process.
+ *  - "device" pointers are CUDA global-memory pointers on the plan's device
+ *    (e.g. torch tensor data_ptr()); "host" pointers are ordinary memory.
+ *    The caller owns every buffer it passes; the plan owns its tables,
+ *    gains and accumulators.  Host arrays given to create/configure are
+ *    copied before the call returns.
+ *  - Work is enqueued on the plan's stream and is asynchronous unless the
+ *    description says "synchronous".  Device faults surface as
+ *    EPIC_ERR_CUDA on a later call or on epic_plan_sync().
+ *  - A plan is not thread-safe; use one plan per host thread and stream.
+ *  - Complex numbers are interleaved (re, im) pairs.
+ */
+#ifndef EPIC_H
+#define EPIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epic_plan_s* epic_plan_t;
+
+typedef enum {
+  EPIC_OK = 0,
+  EPIC_ERR_INVALID_ARG = 1,    /* bad pointer, size, enum or gamma */
+  EPIC_ERR_GRID_TOO_SMALL = 2, /* a gridding stencil falls outside [0, N) */
+  EPIC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  EPIC_ERR_OOM = 4,            /* device or host allocation failed */
+  EPIC_ERR_NUMERIC = 5,        /* EPICal held antennas (non-finite / tiny D) */
+  EPIC_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+  EPIC_ERR_UNSUPPORTED = 7,    /* valid request this build cannot run */
+  EPIC_ERR_STATE = 8           /* call out of order (e.g. update before image) */
+} epic_status;
+
+typedef enum { EPIC_KERNEL_GAUSSIAN = 0, EPIC_KERNEL_TOPHAT = 1 } epic_kernel_type;
+typedef enum { EPIC_IN_CI4 = 0, EPIC_IN_COMPLEX64 = 1 } epic_input_format;
+typedef enum { EPIC_PREC_FP32 = 0, EPIC_PREC_FP16 = 1, EPIC_PREC_BF16 = 2 } epic_precision;
+
+/* Plan description (Sec. 2.1: antenna positions, grid, kernel, channels). */
+typedef struct {
+  int n_ant;                   /* Na >= 1 */
+  const double* ant_xy_m;      /* host [Na][2]: planar East, North positions, metres */
+  int n_chan;                  /* C >= 1 */
+  const double* freq_hz;       /* host [C]: channel centre frequencies */
+  int grid_n;                  /* N: power of two, 16..128 */
+  double cell_wavelengths;     /* grid cell du in wavelengths (0.5 = full sky) */
+  int kernel;                  /* epic_kernel_type: antenna illumination W_a */
+  int kernel_support;          /* K: odd stencil side in cells, 1..7 */
+  double kernel_param;         /* Gaussian sigma in cells / tophat side in metres */
+  int input;                   /* epic_input_format of the voltages */
+  const float* voltage_scale;  /* host [C] multiplier per channel, or NULL = 1 */
+  const unsigned char* flags;  /* host [Na], 1 = antenna flagged, or NULL */
+  int precision;               /* epic_precision of the FFT; FP32 only here */
+  void* cuda_stream;           /* cudaStream_t for all work; NULL = default */
+} epic_plan_desc;
+
+/* Read-only facts about a plan (epic_plan_get_info). */
+typedef struct {
+  int n_ant, n_chan, grid_n, kernel_support;
+  int window_rows;             /* max over channels of occupied grid rows */
+  int cal_kx, cal_ky;          /* calibrator pixel, -1 before epical_configure */
+  int ctas;                    /* persistent CTAs used by epic_image */
+  int units_per_chan;          /* time segments per channel per call */
+  size_t smem_bytes;           /* dynamic shared memory of the image kernel */
+  long long frames_pending;    /* frames correlated since the last update */
+  long long iteration;         /* completed EPICal updates */
+} epic_plan_info;
+
+/* Build the gridding tables of Eq. 9 for every (channel, antenna): the
+ * stencil centre is the nearest cell to u_a/du + N/2 (u_a = r_a f / c),
+ * taps are normalised to sum 1 (W(0) = 1, Sec. 2.1).  Uploads tables and
+ * sets all gains to 1.  Synchronous.  *out receives the plan.
+ * Errors: INVALID_ARG (sizes, enums, NULL arrays), GRID_TOO_SMALL,
+ * UNSUPPORTED (N or Na outside the built kernels), CUDA, OOM. */
+epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* desc);
+
+/* Free the plan and its device memory (waits for its stream). NULL is OK. */
+epic_status epic_plan_destroy(epic_plan_t plan);
+
+/* Use another stream for subsequent work. */
+epic_status epic_plan_set_stream(epic_plan_t plan, void* cuda_stream);
+
+/* Fill *info.  Host only. */
+epic_status epic_plan_get_info(epic_plan_t plan, epic_plan_info* info);
+
+/* Replace the current gains g_a (Eq. 8 divides by them).  gains: host
+ * [C][Na] complex128.  Zero or non-finite gains give INVALID_ARG.
+ * Synchronous upload. */
+epic_status epic_set_gains(epic_plan_t plan, const double* gains);
+
+/* Image one batch of frames (Eqs. 8-10 and the square-and-average step):
+ * image[c][ky][kx] (+)= (1/n_time) sum_t |E'(s_k, t)|^2 for every channel.
+ * d_volt: device [n_time][C][Na], one byte per sample (EPIC_IN_CI4) or
+ * complex float32 (EPIC_IN_COMPLEX64).  d_image: device [C][N][N] float64,
+ * pixel (N/2, N/2) is the phase centre, l = (kx - N/2)/(N du).
+ * accumulate = 0 overwrites d_image, else adds.  If EPICal is configured
+ * the same pass accumulates K_a and P_a of Eqs. 12 and 15 with the
+ * uncalibrated E_a into the plan.  Asynchronous.
+ * Errors: INVALID_ARG (NULL, n_time < 1), CUDA. */
+epic_status epic_image(epic_plan_t plan, const void* d_volt, long long n_time,
+                       double* d_image, int accumulate);
+
+/* epic_image on host buffers: copies h_volt (layout as d_volt) to the
+ * device, images it and copies the [C][N][N] float64 image back to
+ * h_image.  Uses plan-owned device staging buffers (grown on demand).
+ * Pinned host memory makes the copies faster.  Synchronous. */
+epic_status epic_image_host(epic_plan_t plan, const void* h_volt, long long n_time,
+                            double* h_image, int accumulate);
+
+/* Arm EPICal (Sec. 2.2).  (cal_l, cal_m): calibrator direction; the pixel
+ * used is the nearest pixel centre.  Model: n_src point sources, host
+ * src_lmS [n_src][3] rows (l, m, S) with apparent fluxes S, used for every
+ * channel; V^M_ab = sum_s S_s exp(-2 pi i (u_a - u_b) . s).  The plan
+ * forms D_a = sum_{b != a} conj(A_{0,b}) V^M_ab once (Eq. 16 denominator
+ * over Na), A_{0,a} being the exact response of the calibrator pixel to
+ * antenna a.  gamma in [0, 1) is the damping of Eq. 17.  g0: host [C][Na]
+ * complex128 initial gains or NULL = 1.  Resets the accumulators.
+ * Synchronous.  Errors: INVALID_ARG (gamma, pixel outside the image,
+ * n_src < 1), CUDA. */
+epic_status epical_configure(epic_plan_t plan, double cal_l, double cal_m,
+                             int n_src, const double* src_lmS, double gamma,
+                             const double* g0);
+
+/* EPICal update of Eqs. 15-17 from the frames imaged since the last update:
+ * C_a = <K_a> - conj(A_{0,a}) <P_a> / conj(g_a),
+ * g_a <- (1 - gamma) C_a / D_a + gamma g_a, then clears K, P.  Flagged
+ * antennas, |D_a| below 1e-30 and non-finite results keep the old gain and
+ * are counted (see epic_plan_sync).  d_gains_out: device [C][Na]
+ * complex128 copy of the new gains, or NULL.  d_status: device [C][Na]
+ * int32 (1 = held), or NULL.  Asynchronous.
+ * Errors: STATE (not configured, or no frames since the last update). */
+epic_status epical_update(epic_plan_t plan, double* d_gains_out, int* d_status);
+
+/* Wait for the plan's stream.  *n_held (may be NULL) receives the number
+ * of held (antenna, channel) gains since the previous sync; the call
+ * returns EPIC_ERR_NUMERIC if it is non-zero.  Synchronous. */
+epic_status epic_plan_sync(epic_plan_t plan, int* n_held);
+
+/* Current gains to host [C][Na] complex128.  Synchronous. */
+epic_status epical_get_gains(epic_plan_t plan, double* h_gains);
+
+/* Checkpoint: EPICal state (gains, accumulators, counters) to host.  With
+ * buf == NULL only *bytes is set.  Synchronous. */
+epic_status epical_get_state(epic_plan_t plan, void* buf, size_t* bytes);
+
+/* Resume from epical_get_state output of a plan with the same C and Na.
+ * Errors: INVALID_ARG (size or header mismatch).  Synchronous. */
+epic_status epical_set_state(epic_plan_t plan, const void* buf, size_t bytes);
+
+/* Debug/test accessors (synchronous, host outputs). */
+/* base_xy: host [C][Na][2] int32 stencil-centre cell (x, y); w: host
+ * [C][Na][K][K] float64 normalised tap weights ([dy][dx]); either may be
+ * NULL.  Flagged antennas have zero weights. */
+epic_status epic_plan_get_grid_table(epic_plan_t plan, int* base_xy, double* w);
+
+/* Unpack n 4-bit complex bytes (device d_in) to device float32 pairs
+ * d_out [n][2] exactly (high nibble real, low nibble imaginary, two's
+ * complement).  Asynchronous. */
+epic_status epic_unpack_ci4(epic_plan_t plan, const unsigned char* d_in, float* d_out,
+                            long long n);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* epic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIC_H */

@@ -1,0 +1,240 @@
+"""Python binding of the EPIC/EPICal C ABI.
+
+Thin wrappers with the C names (epic_plan_create, epic_image, epical_update,
+...) plus a `Plan` object that owns the handle.  torch tensors provide device
+memory and the CUDA stream; all computation is in libepic.so.  If the
+library is missing the calls raise: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import EpicError  # noqa: F401
+
+_KERNELS = {"gaussian": B.EPIC_KERNEL_GAUSSIAN, "tophat": B.EPIC_KERNEL_TOPHAT}
+_INPUTS = {"ci4": B.EPIC_IN_CI4, "c64": B.EPIC_IN_COMPLEX64}
+
+
+def _torch():
+    import torch  # deferred so that non-GPU users of the module need not import it
+    return torch
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _c128_as_f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.complex128).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} complex values, got {a.size}")
+    return a.view(np.float64)
+
+
+class Plan:
+    """One EPIC/EPICal plan: array, grid, kernel and channels (Sec. 2.1)."""
+
+    def __init__(self, ant_xy_m, freq_hz, grid_n, cell=0.5, kernel="gaussian", support=3,
+                 param=0.5, input="ci4", voltage_scale=None, flags=None, stream=None):
+        lib = B.load()
+        self._lib = lib
+        self.ant = _f64(ant_xy_m).reshape(-1, 2)
+        self.freqs = _f64(freq_hz).reshape(-1)
+        self.n_ant, self.n_chan, self.grid_n = self.ant.shape[0], self.freqs.size, int(grid_n)
+        self.input = input
+        self._vs = None if voltage_scale is None else np.ascontiguousarray(voltage_scale, np.float32)
+        self._fl = None if flags is None else np.ascontiguousarray(np.asarray(flags) != 0, np.uint8)
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        d = B.PlanDesc()
+        d.n_ant = self.n_ant
+        d.ant_xy_m = self.ant.ctypes.data_as(B.c_dp)
+        d.n_chan = self.n_chan
+        d.freq_hz = self.freqs.ctypes.data_as(B.c_dp)
+        d.grid_n = self.grid_n
+        d.cell_wavelengths = float(cell)
+        d.kernel = _KERNELS[kernel]
+        d.kernel_support = int(support)
+        d.kernel_param = float(param)
+        d.input = _INPUTS[input]
+        d.voltage_scale = None if self._vs is None else self._vs.ctypes.data_as(B.c_fp)
+        d.flags = None if self._fl is None else self._fl.ctypes.data_as(B.c_u8p)
+        d.precision = B.EPIC_PREC_FP32
+        d.cuda_stream = ct.c_void_p(int(stream))
+        h = ct.c_void_p()
+        B.check(lib.epic_plan_create(ct.byref(h), ct.byref(d)))
+        self.handle = h
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.epic_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- wrappers ----
+    def set_stream(self, stream):
+        B.check(self._lib.epic_plan_set_stream(self.handle, ct.c_void_p(int(stream))))
+
+    def info(self) -> dict:
+        i = B.PlanInfo()
+        B.check(self._lib.epic_plan_get_info(self.handle, ct.byref(i)))
+        return {k: getattr(i, k) for k, _ in B.PlanInfo._fields_}
+
+    def set_gains(self, gains):
+        g = _c128_as_f64(gains, self.n_chan * self.n_ant)
+        B.check(self._lib.epic_set_gains(self.handle, g.ctypes.data_as(B.c_dp)))
+
+    def image(self, volt, image=None, accumulate=False):
+        """Image a device voltage batch [T][C][Na] (uint8 ci4 or complex64)
+        into image [C][N][N] float64 (allocated if None)."""
+        torch = _torch()
+        want = torch.uint8 if self.input == "ci4" else torch.complex64
+        if volt.dim() != 3 or volt.shape[1] != self.n_chan or volt.shape[2] != self.n_ant:
+            raise ValueError("volt must be [T][C][Na]")
+        if image is None:
+            image = torch.empty((self.n_chan, self.grid_n, self.grid_n), dtype=torch.float64,
+                                device=volt.device)
+        B.check(self._lib.epic_image(self.handle, _dptr(volt, want, "volt"), int(volt.shape[0]),
+                                     _dptr(image, torch.float64, "image"), int(bool(accumulate))))
+        return image
+
+    def image_host(self, volt, image=None, accumulate=False):
+        """Host-buffer form (copies inside the call).  volt: numpy array or
+        CPU tensor [T][C][Na]; returns a float64 [C][N][N] numpy image."""
+        torch = _torch()
+        if isinstance(volt, torch.Tensor):
+            if volt.is_cuda:
+                raise TypeError("image_host takes host memory")
+            vt = volt.contiguous()
+            vptr = ct.c_void_p(vt.data_ptr())
+            T = vt.shape[0]
+        else:
+            vt = np.ascontiguousarray(volt)
+            vptr = ct.c_void_p(vt.ctypes.data)
+            T = vt.shape[0]
+        if image is None:
+            image = np.zeros((self.n_chan, self.grid_n, self.grid_n), np.float64)
+        if isinstance(image, torch.Tensor):
+            iptr = ct.c_void_p(image.data_ptr())
+        else:
+            iptr = ct.c_void_p(image.ctypes.data)
+        B.check(self._lib.epic_image_host(self.handle, vptr, int(T), iptr, int(bool(accumulate))))
+        return image
+
+    def configure(self, cal_lm, model_lmS, gamma, g0=None):
+        src = _f64(model_lmS).reshape(-1, 3)
+        g = None if g0 is None else _c128_as_f64(g0, self.n_chan * self.n_ant)
+        B.check(self._lib.epical_configure(
+            self.handle, float(cal_lm[0]), float(cal_lm[1]), src.shape[0],
+            src.ctypes.data_as(B.c_dp), float(gamma),
+            None if g is None else g.ctypes.data_as(B.c_dp)))
+
+    def update(self, gains_out=None, status=None):
+        torch = _torch()
+        B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),
+                                        _dptr(status, torch.int32, "status")))
+
+    def sync(self) -> int:
+        """Wait for the stream; return the number of gains held since the
+        last sync (EPIC_ERR_NUMERIC is reported through the count)."""
+        n = ct.c_int(0)
+        st = self._lib.epic_plan_sync(self.handle, ct.byref(n))
+        if st not in (B.EPIC_OK, 5):
+            B.check(st)
+        return n.value
+
+    def gains(self) -> np.ndarray:
+        out = np.zeros((self.n_chan, self.n_ant), np.complex128)
+        B.check(self._lib.epical_get_gains(self.handle, out.view(np.float64).ctypes.data_as(B.c_dp)))
+        return out
+
+    def get_state(self) -> bytes:
+        n = ct.c_size_t(0)
+        B.check(self._lib.epical_get_state(self.handle, None, ct.byref(n)))
+        buf = ct.create_string_buffer(n.value)
+        B.check(self._lib.epical_get_state(self.handle, buf, ct.byref(n)))
+        return buf.raw
+
+    def set_state(self, state: bytes):
+        buf = ct.create_string_buffer(state, len(state))
+        B.check(self._lib.epical_set_state(self.handle, buf, len(state)))
+
+    def grid_table(self):
+        K = None
+        base = np.zeros((self.n_chan, self.n_ant, 2), np.int32)
+        B.check(self._lib.epic_plan_get_grid_table(self.handle, base.ctypes.data_as(B.c_ip), None))
+        info = self.info()
+        K = info["kernel_support"]
+        w = np.zeros((self.n_chan, self.n_ant, K, K), np.float64)
+        B.check(self._lib.epic_plan_get_grid_table(self.handle, None, w.ctypes.data_as(B.c_dp)))
+        return base, w
+
+    def unpack_ci4(self, d_in, d_out=None):
+        torch = _torch()
+        if d_out is None:
+            d_out = torch.empty((d_in.numel(), 2), dtype=torch.float32, device=d_in.device)
+        B.check(self._lib.epic_unpack_ci4(self.handle, _dptr(d_in, torch.uint8, "d_in"),
+                                          _dptr(d_out, torch.float32, "d_out"), int(d_in.numel())))
+        return d_out
+
+
+# C-ABI-named module functions (thin aliases of the Plan methods)
+def epic_plan_create(*args, **kw) -> Plan:
+    return Plan(*args, **kw)
+
+
+def epic_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def epic_image(plan: Plan, volt, image=None, accumulate=False):
+    return plan.image(volt, image, accumulate)
+
+
+def epic_image_host(plan: Plan, volt, image=None, accumulate=False):
+    return plan.image_host(volt, image, accumulate)
+
+
+def epical_configure(plan: Plan, cal_lm, model_lmS, gamma, g0=None):
+    return plan.configure(cal_lm, model_lmS, gamma, g0)
+
+
+def epical_update(plan: Plan, gains_out=None, status=None):
+    return plan.update(gains_out, status)
+
+
+def epic_plan_sync(plan: Plan) -> int:
+    return plan.sync()

@@ -1,0 +1,72 @@
+// Internal interface between the host plan (epic_plan.cpp) and the CUDA
+// kernels (epic_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace epic {
+
+// Arguments of one fused imaging launch (gain correction, gridding, 2D FFT,
+// square-accumulate and the EPICal correlation for every frame of a batch).
+struct ImageArgs {
+  const void* volt;        // device [T][C][Na] u8 (ci4) or float2
+  int input_fmt;           // 0 = ci4, 1 = complex64
+  long long n_time;        // T
+  int n_chan, n_ant;       // C, Na
+  int support;             // K
+  const int* cell0;        // [C][Na] window cell of tap (0,0); -1 = flagged
+  const float* wts;        // [C][Na][K*K] weights * (-1)^(jx+jy) / Na
+  const float2* wgain;     // [C][Na] 1/g (gain correction multiplier)
+  const float* vscale;     // [C] voltage scale, or nullptr
+  const int2* win;         // [C] (first occupied grid row y0, occupied rows R)
+  const float2* twid;      // [N] e^{+2 pi i m / N}
+  double* image;           // [C][N][N] accumulated with img_scale
+  double img_scale;        // 1 / T_call
+  int do_cal;              // accumulate K, P
+  int k0x, k0y;            // calibrator pixel
+  float pix_sign;          // (-1)^(k0x+k0y): centring factor of the image
+  double2* kacc;           // [C][Na] sum_t E_a conj(P(t))
+  double* pacc;            // [C][Na] sum_t |E_a|^2
+  int segs;                // time segments per channel (units = C * segs)
+  int rows_alloc;          // shared-memory grid rows (max R)
+  int rs;                  // row stride of the transposed buffer
+  int grid;                // CTAs launched
+  size_t smem;             // dynamic shared memory bytes
+};
+
+// Shape facts of the fused image kernel for grid side n.
+struct ImageKernelShape {
+  int threads;             // CTA size
+  int groups;              // 1-D FFTs in flight per CTA
+  int max_ant;             // largest Na the kernel holds in registers
+};
+
+bool image_kernel_shape(int n, ImageKernelShape* out);
+int image_rs(int rows_alloc);
+size_t image_smem_bytes(int n, int rows_alloc, int rs);
+// Opt in to the shared memory and report resident CTAs per SM.
+cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas_per_sm);
+cudaError_t launch_image(int n, const ImageArgs& a, cudaStream_t s);
+
+struct UpdateArgs {
+  int n_chan, n_ant;
+  double2* kacc;           // [C][Na], cleared by the update
+  double* pacc;            // [C][Na], cleared by the update
+  double inv_frames;       // 1 / frames accumulated
+  const double2* a0;       // [C][Na] A_{0,a}
+  const double2* dden;     // [C][Na] D_a
+  double2* gain;           // [C][Na] g (updated in place)
+  float2* wgain;           // [C][Na] 1/g as float2 (updated)
+  const unsigned char* flags;  // [Na]
+  double gamma;
+  double dmin;
+  double2* gout;           // [C][Na] or nullptr
+  int* status;             // [C][Na] or nullptr
+  int* held_count;         // device counter
+};
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+
+cudaError_t launch_unpack(const unsigned char* in, float2* out, long long n, cudaStream_t s);
+
+}  // namespace epic

@@ -1,0 +1,524 @@
+// CUDA kernels of the EPIC imaging chain and the EPICal update (sm_103a).
+//
+// epic_image_fused<N>: one persistent launch images every frame (t, c) of a
+// batch.  A CTA owns one work unit (channel c, a contiguous time segment) at
+// a time and keeps that unit's running |E(s_k)|^2 sums in registers, so the
+// only HBM traffic per frame is the Na voltage bytes.  Per frame:
+//   A  unpack 4-bit voltages, multiply by 1/g (Eq. 8) and scatter the K x K
+//      weighted taps (Eq. 9) into a shared-memory grid window that spans only
+//      the occupied grid rows; lanes of a warp that hit the same cell are
+//      merged with __match_any_sync before the shared-memory atomic add;
+//   B  EPICal correlation of the previous frame (Eqs. 12, 15), then N-point
+//      row FFTs of the occupied rows, written transposed;
+//   C  N-point column FFTs (Eq. 10), |E|^2 accumulated in registers; the
+//      thread that owns the calibrator pixel stores it for the correlation.
+// The centring factor (-1)^(jx+jy) and the 1/Na of Eq. 10 are folded into
+// the gridding weights by the plan; (-1)^(kx+ky) only matters for the
+// calibrator pixel and is applied there.
+//
+// Each 1-D FFT of length N = N1 * N2 runs on a group of N1 lanes of one warp
+// holding N2 points each: an N2-point DFT in registers, a twiddle
+// e^{+2 pi i n1 k2 / N}, one exchange through shared memory, and N2/N1
+// N1-point DFTs (the four-step decomposition).  Twiddles come from an FP64
+// host table rounded to float.
+#include "epic_internal.h"
+
+#include <cstdint>
+
+namespace epic {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// cos(2 pi m / 32) for m in [0, 8]: exact mathematical constants.
+__host__ __device__ constexpr float cos32_q(int m) {
+  return m == 0 ? 1.0f
+       : m == 1 ? 0.98078528040323044913f
+       : m == 2 ? 0.92387953251128675613f
+       : m == 3 ? 0.83146961230254523708f
+       : m == 4 ? 0.70710678118654752440f
+       : m == 5 ? 0.55557023301960222474f
+       : m == 6 ? 0.38268343236508977173f
+       : m == 7 ? 0.19509032201612826785f
+       : 0.0f;
+}
+// cos(2 pi m / 32) for any integer m, by symmetry.
+__host__ __device__ constexpr float cos32(int m) {
+  return ((m % 32) + 32) % 32 > 16 ? cos32(32 - (((m % 32) + 32) % 32))
+       : ((m % 32) + 32) % 32 > 8 ? -cos32_q(16 - (((m % 32) + 32) % 32))
+       : cos32_q(((m % 32) + 32) % 32);
+}
+
+// v * e^{+2 pi i k / R}; k is a compile-time constant after unrolling.
+template <int R>
+__device__ __forceinline__ float2 twiddle(float2 v, int k) {
+  const int m = ((k * (32 / R)) % 32 + 32) % 32;
+  if (m == 0) return v;
+  if (m == 8) return make_float2(-v.y, v.x);
+  if (m == 16) return make_float2(-v.x, -v.y);
+  if (m == 24) return make_float2(v.y, -v.x);
+  return cmul(v, make_float2(cos32(m), cos32(8 - m)));
+}
+
+// In-register DFT with the '+' sign of Eq. 10, natural order in and out
+// (radix-2 decimation in time, fully unrolled).
+template <int R>
+struct Dft {
+  static __device__ __forceinline__ void run(float2 (&x)[R]) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    Dft<R / 2>::run(e);
+    Dft<R / 2>::run(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      const float2 t = twiddle<R>(o[k], k);
+      x[k] = cadd(e[k], t);
+      x[k + R / 2] = csub(e[k], t);
+    }
+  }
+};
+template <>
+struct Dft<1> {
+  static __device__ __forceinline__ void run(float2 (&)[1]) {}
+};
+
+// Per-N launch shape: N1 lanes per 1-D FFT, N2 points per lane, BT threads.
+template <int N> struct Cfg;
+template <> struct Cfg<16>  { static constexpr int N1 = 4, N2 = 4,  BT = 64; };
+template <> struct Cfg<32>  { static constexpr int N1 = 4, N2 = 8,  BT = 128; };
+template <> struct Cfg<64>  { static constexpr int N1 = 8, N2 = 8,  BT = 512; };
+template <> struct Cfg<128> { static constexpr int N1 = 8, N2 = 16, BT = 512; };
+
+constexpr int kMaxAntPerThread = 4;
+
+template <int N>
+struct Geo {
+  static constexpr int N1 = Cfg<N>::N1, N2 = Cfg<N>::N2, BT = Cfg<N>::BT;
+  static constexpr int GROUPS = BT / N1;
+  static constexpr int COLROUNDS = N / GROUPS;
+  static constexpr int NACC = COLROUNDS * N2;
+  static constexpr int H = N2 / N1;
+  static constexpr int ZS = N1 + 1;                       // padded exchange row
+  static constexpr int ZG0 = N2 * ZS;
+  static constexpr int ZG = ZG0 + ((8 - ZG0 % 16) + 16) % 16;  // group stride
+  static_assert(N1 * N2 == N, "N1*N2 must be N");
+  static_assert(N2 % N1 == 0, "N2 must be a multiple of N1");
+  static_assert(N % GROUPS == 0, "columns must split evenly over groups");
+  static_assert(32 % N1 == 0, "FFT groups must tile a warp");
+};
+
+// 1-D FFT of length N on a group of N1 lanes.
+// In:  v[j] = x[n1 + N1 j], j < N2.
+// Out: v[h N1 + k1] = X[n1 + N1 h + N2 k1] with X[k] = sum_n x[n] e^{+2 pi i n k / N}.
+template <int N>
+__device__ __forceinline__ void fft_group(float2 (&v)[Geo<N>::N2], int n1, float2* z,
+                                          const float2* tw, unsigned gmask) {
+  constexpr int N1 = Geo<N>::N1, N2 = Geo<N>::N2, ZS = Geo<N>::ZS, H = Geo<N>::H;
+  Dft<N2>::run(v);
+#pragma unroll
+  for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) z[k2 * ZS + n1] = v[k2];
+  __syncwarp(gmask);
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    float2 u[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) u[m] = z[(n1 + N1 * h) * ZS + m];
+    Dft<N1>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[h * N1 + k1] = u[k1];
+  }
+  __syncwarp(gmask);
+}
+
+__device__ __forceinline__ float2 load_volt(const ImageArgs& A, long long t, int c, int a) {
+  const size_t idx = (static_cast<size_t>(t) * A.n_chan + c) * A.n_ant + a;
+  if (A.input_fmt == 0) {
+    const unsigned b = __ldg(static_cast<const unsigned char*>(A.volt) + idx);
+    const int re = static_cast<int>(b << 24) >> 28;
+    const int im = static_cast<int>(b << 28) >> 28;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+  return __ldg(static_cast<const float2*>(A.volt) + idx);
+}
+
+template <int N, int MAXA>
+__global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
+  using G = Geo<N>;
+  constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][N] grid window
+  float2* Tt = Wg + A.rows_alloc * N;                  // [N][rs] row spectra, transposed
+  float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
+  float2* tw = Z + GROUPS * G::ZG;                     // [N] twiddles
+  float2* pixs = tw + N;                               // calibrator pixel
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int g = tid / N1;
+  const int n1 = tid % N1;
+  const unsigned gmask = (N1 == 32) ? kFull : (((1u << N1) - 1u) << (lane & ~(N1 - 1)));
+  float2* zg = Z + g * G::ZG;
+
+  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
+  for (int i = tid; i < A.rows_alloc * N; i += BT) Wg[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const int Na = A.n_ant;
+  const int K = A.support;
+  const int KK = K * K;
+  const int items = K * Na;
+  const int items_pad = ((items + BT - 1) / BT) * BT;
+  const long long T = A.n_time;
+  const int units = A.n_chan * A.segs;
+
+  // calibrator pixel: column round, group, lane and register slot
+  const int pr = A.k0x / GROUPS, pg = A.k0x % GROUPS;
+  const int pn1 = A.k0y % N1;
+  const int pq = A.k0y / N1;
+  const int pslot = (pq % H) * N1 + pq / H;
+  const bool pix_owner = A.do_cal && g == pg && n1 == pn1;
+
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int c = u / A.segs;
+    const int s = u - c * A.segs;
+    const long long t0 = T * s / A.segs;
+    const long long t1 = T * (s + 1) / A.segs;
+    if (t0 >= t1) continue;
+    const int2 wn = __ldg(A.win + c);
+    const int y0 = wn.x, R = wn.y;
+    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+    const int* cell0 = A.cell0 + static_cast<size_t>(c) * Na;
+    const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
+    const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
+
+    float acc[G::NACC];
+#pragma unroll
+    for (int i = 0; i < G::NACC; ++i) acc[i] = 0.f;
+    float2 kac[MAXA], ecur[MAXA];
+    float pac[MAXA];
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      kac[i] = make_float2(0.f, 0.f);
+      ecur[i] = make_float2(0.f, 0.f);
+      pac[i] = 0.f;
+    }
+
+    for (long long t = t0; t < t1; ++t) {
+      // ---- A: raw voltages for the correlation, then gain + scatter ----
+      float2 eprev[MAXA];
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        eprev[i] = ecur[i];
+        const int a = tid + BT * i;
+        if (A.do_cal && a < Na) {
+          const float2 e = load_volt(A, t, c, a);
+          ecur[i] = make_float2(e.x * vs, e.y * vs);
+        }
+      }
+      for (int it = tid; it < items_pad; it += BT) {
+        const bool in = it < items;
+        const int a = in ? it % Na : 0;
+        const int dy = in ? it / Na : 0;
+        const int c0 = in ? __ldg(cell0 + a) : -1;
+        const bool valid = c0 >= 0;
+        float2 ec = make_float2(0.f, 0.f);
+        if (valid) {
+          const float2 e = load_volt(A, t, c, a);
+          ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
+        }
+        const int rowcell = valid ? c0 + dy * N : -1 - lane;
+        const unsigned peers = __match_any_sync(kFull, rowcell);
+        const bool dup = __popc(peers) > 1;
+        const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
+        if (!__any_sync(kFull, dup)) {
+          if (valid) {
+            for (int dx = 0; dx < K; ++dx) {
+              const float w = __ldg(wrow + dx);
+              atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
+              atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
+            }
+          }
+        } else {
+          // lanes sharing a cell: the lowest lane adds the group's sum
+          const int leader = __ffs(peers) - 1;
+          for (int dx = 0; dx < K; ++dx) {
+            const float w = valid ? __ldg(wrow + dx) : 0.f;
+            const float vx = w * ec.x, vy = w * ec.y;
+            float sx = 0.f, sy = 0.f;
+#pragma unroll
+            for (int src = 0; src < 32; ++src) {
+              const float ox = __shfl_sync(kFull, vx, src);
+              const float oy = __shfl_sync(kFull, vy, src);
+              if ((peers >> src) & 1u) {
+                sx += ox;
+                sy += oy;
+              }
+            }
+            if (valid && lane == leader) {
+              atomicAdd(&Wg[rowcell + dx].x, sx);
+              atomicAdd(&Wg[rowcell + dx].y, sy);
+            }
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- B: correlation of the previous frame, then row FFTs ----
+      if (A.do_cal && t > t0) {
+        const float2 p = pixs[0];
+#pragma unroll
+        for (int i = 0; i < MAXA; ++i) {
+          const float2 e = eprev[i];
+          kac[i].x += e.x * p.x + e.y * p.y;
+          kac[i].y += e.y * p.x - e.x * p.y;
+          pac[i] += e.x * e.x + e.y * e.y;
+        }
+      }
+      for (int row = g; row < R; row += GROUPS) {
+        float2 v[N2];
+        float2* wr = Wg + row * N;
+#pragma unroll
+        for (int j = 0; j < N2; ++j) v[j] = wr[n1 + N1 * j];
+#pragma unroll
+        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+        fft_group<N>(v, n1, zg, tw, gmask);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const int kx = n1 + N1 * h + N2 * k1;
+            Tt[kx * A.rs + row] = v[h * N1 + k1];
+          }
+      }
+      __syncthreads();
+
+      // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
+#pragma unroll
+      for (int r = 0; r < G::COLROUNDS; ++r) {
+        const int kx = g + GROUPS * r;
+        float2 v[N2];
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const int jw = n1 + N1 * j - y0;
+          v[j] = (jw >= 0 && jw < R) ? Tt[kx * A.rs + jw] : make_float2(0.f, 0.f);
+        }
+        fft_group<N>(v, n1, zg, tw, gmask);
+#pragma unroll
+        for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
+        if (pix_owner && r == pr) {
+#pragma unroll
+          for (int q = 0; q < N2; ++q)
+            if (q == pslot) pixs[0] = make_float2(v[q].x * A.pix_sign, v[q].y * A.pix_sign);
+        }
+      }
+    }
+    __syncthreads();
+
+    // correlation of the unit's last frame
+    if (A.do_cal) {
+      const float2 p = pixs[0];
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const float2 e = ecur[i];
+        kac[i].x += e.x * p.x + e.y * p.y;
+        kac[i].y += e.y * p.x - e.x * p.y;
+        pac[i] += e.x * e.x + e.y * e.y;
+      }
+    }
+
+    // flush the unit's partial sums (FP32 over one segment, FP64 across)
+    double* img = A.image + static_cast<size_t>(c) * N * N;
+#pragma unroll
+    for (int r = 0; r < G::COLROUNDS; ++r) {
+      const int kx = g + GROUPS * r;
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const int ky = n1 + N1 * h + N2 * k1;
+          atomicAdd(img + ky * N + kx, static_cast<double>(acc[r * N2 + h * N1 + k1]) * A.img_scale);
+        }
+    }
+    if (A.do_cal) {
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const int a = tid + BT * i;
+        if (a < Na && cell0[a] >= 0) {
+          const size_t o = static_cast<size_t>(c) * Na + a;
+          atomicAdd(&A.kacc[o].x, static_cast<double>(kac[i].x));
+          atomicAdd(&A.kacc[o].y, static_cast<double>(kac[i].y));
+          atomicAdd(A.pacc + o, static_cast<double>(pac[i]));
+        }
+      }
+    }
+  }
+}
+
+// EPICal update (Eqs. 15-17) in FP64, one thread per (channel, antenna).
+__global__ void epical_update_kernel(const UpdateArgs A) {
+  const int n = A.n_chan * A.n_ant;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int a = i % A.n_ant;
+  const double2 k = A.kacc[i];
+  const double kx = k.x * A.inv_frames, ky = k.y * A.inv_frames;
+  const double pb = A.pacc[i] * A.inv_frames;
+  const double2 g = A.gain[i];
+  const double2 a0 = A.a0[i];
+  const double2 d = A.dden[i];
+  // q = conj(A0) * P / conj(g)
+  const double nr = a0.x * pb, ni = -a0.y * pb;   // conj(A0) * P
+  const double gr = g.x, gi = -g.y;               // conj(g)
+  const double gg = gr * gr + gi * gi;
+  const double qr = (nr * gr + ni * gi) / gg;
+  const double qi = (ni * gr - nr * gi) / gg;
+  const double cr = kx - qr, ci = ky - qi;        // C_a (Eq. 15)
+  const double dd = d.x * d.x + d.y * d.y;
+  const double sr = (cr * d.x + ci * d.y) / dd;   // C / D (Eq. 16)
+  const double si = (ci * d.x - cr * d.y) / dd;
+  const double one_m = 1.0 - A.gamma;
+  const double nxr = one_m * sr + A.gamma * g.x;  // Eq. 17
+  const double nxi = one_m * si + A.gamma * g.y;
+  const bool held = A.flags[a] != 0 || !(dd > A.dmin * A.dmin) || !isfinite(nxr) ||
+                    !isfinite(nxi) || (nxr == 0.0 && nxi == 0.0);
+  double2 out = g;
+  if (!held) {
+    out = make_double2(nxr, nxi);
+    A.gain[i] = out;
+    const double m2 = nxr * nxr + nxi * nxi;
+    A.wgain[i] = make_float2(static_cast<float>(nxr / m2), static_cast<float>(-nxi / m2));
+  }
+  if (A.status) A.status[i] = held ? 1 : 0;
+  if (held && !A.flags[a]) atomicAdd(A.held_count, 1);
+  if (A.gout) A.gout[i] = out;
+  A.kacc[i] = make_double2(0.0, 0.0);
+  A.pacc[i] = 0.0;
+}
+
+__global__ void unpack_ci4_kernel(const unsigned char* __restrict__ in, float2* __restrict__ out,
+                                  long long n) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += stride) {
+    const unsigned b = in[i];
+    const int re = static_cast<int>(b << 24) >> 28;
+    const int im = static_cast<int>(b << 28) >> 28;
+    out[i] = make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+}
+
+template <int N, int MAXA>
+cudaError_t prepare_nm(size_t smem, int* ctas) {
+  cudaError_t e = cudaFuncSetAttribute(epic_image_fused<N, MAXA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, epic_image_fused<N, MAXA>,
+                                                       Cfg<N>::BT, smem);
+}
+
+// One antenna per thread when Na <= CTA size, else up to kMaxAntPerThread.
+template <int N>
+cudaError_t prepare_n(size_t smem, int n_ant, int* ctas) {
+  if (n_ant <= Cfg<N>::BT) return prepare_nm<N, 1>(smem, ctas);
+  return prepare_nm<N, kMaxAntPerThread>(smem, ctas);
+}
+
+template <int N>
+cudaError_t launch_n(const ImageArgs& a, cudaStream_t s) {
+  if (a.n_ant <= Cfg<N>::BT)
+    epic_image_fused<N, 1><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  else
+    epic_image_fused<N, kMaxAntPerThread><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+void shape_n(ImageKernelShape* o) {
+  o->threads = Cfg<N>::BT;
+  o->groups = Geo<N>::GROUPS;
+  o->max_ant = Cfg<N>::BT * kMaxAntPerThread;
+}
+
+}  // namespace
+
+bool image_kernel_shape(int n, ImageKernelShape* out) {
+  switch (n) {
+    case 16: shape_n<16>(out); return true;
+    case 32: shape_n<32>(out); return true;
+    case 64: shape_n<64>(out); return true;
+    case 128: shape_n<128>(out); return true;
+    default: return false;
+  }
+}
+
+int image_rs(int rows_alloc) {
+  int rs = rows_alloc;
+  while (rs % 16 != 4) ++rs;
+  return rs;
+}
+
+size_t image_smem_bytes(int n, int rows_alloc, int rs) {
+  int groups = 0, zg = 0;
+  switch (n) {
+    case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
+    case 32: groups = Geo<32>::GROUPS; zg = Geo<32>::ZG; break;
+    case 64: groups = Geo<64>::GROUPS; zg = Geo<64>::ZG; break;
+    case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
+    default: return 0;
+  }
+  const size_t elems = static_cast<size_t>(rows_alloc) * n + static_cast<size_t>(n) * rs +
+                       static_cast<size_t>(groups) * zg + n + 2;
+  return elems * sizeof(float2);
+}
+
+cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas) {
+  switch (n) {
+    case 16: return prepare_n<16>(smem, n_ant, ctas);
+    case 32: return prepare_n<32>(smem, n_ant, ctas);
+    case 64: return prepare_n<64>(smem, n_ant, ctas);
+    case 128: return prepare_n<128>(smem, n_ant, ctas);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_image(int n, const ImageArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 16: return launch_n<16>(a, s);
+    case 32: return launch_n<32>(a, s);
+    case 64: return launch_n<64>(a, s);
+    case 128: return launch_n<128>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
+  const int n = a.n_chan * a.n_ant;
+  const int bt = 256;
+  epical_update_kernel<<<(n + bt - 1) / bt, bt, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const unsigned char* in, float2* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int bt = 256;
+  long long blocks = (n + bt - 1) / bt;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  unpack_ci4_kernel<<<static_cast<unsigned>(blocks), bt, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace epic

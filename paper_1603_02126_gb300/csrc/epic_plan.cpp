@@ -1,0 +1,698 @@
+// Host side of the EPIC/EPICal C ABI: plan validation, FP64 table
+// construction, device memory, launches.  See include/epic.h.
+#include "../../include/epic.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "epic_internal.h"
+
+namespace {
+
+constexpr double kC = 299792458.0;  // speed of light, m/s
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kDmin = 1e-30;     // |D_a| at or below this holds the gain
+
+thread_local std::string g_last_error;
+
+epic_status fail(epic_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+epic_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(EPIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define EPIC_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    release();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    else p = nullptr;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct epic_plan_s {
+  // description
+  int na = 0, nc = 0, n = 0, k = 0, input = 0, kernel = 0;
+  double cell = 0.5, kparam = 0.5;
+  std::vector<double> ant;      // [Na][2]
+  std::vector<double> freq;     // [C]
+  std::vector<float> vscale;    // [C]
+  std::vector<unsigned char> flags;  // [Na]
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // host tables (FP64, as computed)
+  std::vector<int> base;        // [C][Na][2]
+  std::vector<double> w64;      // [C][Na][K*K]
+  std::vector<int> y0, rows;    // [C]
+  int rows_alloc = 0;
+
+  // device tables
+  DevBuf<int> d_cell0;          // [C][Na]
+  DevBuf<float> d_wts;          // [C][Na][K*K] folded
+  DevBuf<float2> d_wgain;       // [C][Na] 1/g
+  DevBuf<double2> d_gain;       // [C][Na] g
+  DevBuf<float> d_vscale;       // [C]
+  DevBuf<int2> d_win;           // [C]
+  DevBuf<float2> d_twid;        // [N]
+  DevBuf<unsigned char> d_flags;  // [Na]
+
+  // EPICal
+  bool cal = false;
+  int k0x = -1, k0y = -1;
+  double gamma = 0.5;
+  DevBuf<double2> d_a0, d_dden, d_kacc;
+  DevBuf<double> d_pacc;
+  DevBuf<int> d_held;
+  long long frames = 0;
+  long long iteration = 0;
+
+  // launch shape
+  epic::ImageKernelShape shape{};
+  size_t smem = 0;
+  int rs = 0;
+  int ctas = 0;
+  int sms = 0;
+
+  // host-API staging
+  DevBuf<unsigned char> d_stage_in;
+  DevBuf<double> d_stage_img;
+};
+
+namespace {
+
+epic_status check_plan(epic_plan_t p) {
+  if (!p) return fail(EPIC_ERR_INVALID_ARG, "plan is NULL");
+  return EPIC_OK;
+}
+
+// Segments per channel: enough work units to fill every CTA a few times,
+// preferring a total that is a multiple of the CTA count.
+int choose_segments(int n_chan, long long n_time, int ctas) {
+  long long best = 1;
+  const long long min_len = 16;
+  for (long long s = 1; s <= 4096; ++s) {
+    if (n_time / s < min_len && s > 1) break;
+    best = s;
+    const long long units = static_cast<long long>(n_chan) * s;
+    if (units >= 4LL * ctas && units % ctas == 0) return static_cast<int>(s);
+    if (units >= 16LL * ctas) return static_cast<int>(s);
+  }
+  return static_cast<int>(best);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* epic_last_error(void) { return g_last_error.c_str(); }
+
+epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
+  if (!out || !d) return fail(EPIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->n_ant < 1 || d->n_chan < 1) return fail(EPIC_ERR_INVALID_ARG, "n_ant and n_chan must be >= 1");
+  if (!d->ant_xy_m || !d->freq_hz) return fail(EPIC_ERR_INVALID_ARG, "ant_xy_m and freq_hz are required");
+  if (!is_pow2(d->grid_n) || d->grid_n < 16)
+    return fail(EPIC_ERR_INVALID_ARG, "grid_n must be a power of two >= 16");
+  if (!(d->cell_wavelengths > 0) || !std::isfinite(d->cell_wavelengths))
+    return fail(EPIC_ERR_INVALID_ARG, "cell_wavelengths must be > 0");
+  if (d->kernel_support < 1 || d->kernel_support > 7 || d->kernel_support % 2 == 0)
+    return fail(EPIC_ERR_INVALID_ARG, "kernel_support must be odd, 1..7");
+  if (d->kernel != EPIC_KERNEL_GAUSSIAN && d->kernel != EPIC_KERNEL_TOPHAT)
+    return fail(EPIC_ERR_INVALID_ARG, "unknown kernel type");
+  if (!(d->kernel_param > 0) || !std::isfinite(d->kernel_param))
+    return fail(EPIC_ERR_INVALID_ARG, "kernel_param must be > 0");
+  if (d->input != EPIC_IN_CI4 && d->input != EPIC_IN_COMPLEX64)
+    return fail(EPIC_ERR_INVALID_ARG, "unknown input format");
+  if (d->precision != EPIC_PREC_FP32)
+    return fail(EPIC_ERR_UNSUPPORTED, "only EPIC_PREC_FP32 is built");
+  for (int c = 0; c < d->n_chan; ++c)
+    if (!(d->freq_hz[c] > 0) || !std::isfinite(d->freq_hz[c]))
+      return fail(EPIC_ERR_INVALID_ARG, "frequencies must be finite and > 0");
+  for (int i = 0; i < 2 * d->n_ant; ++i)
+    if (!std::isfinite(d->ant_xy_m[i])) return fail(EPIC_ERR_INVALID_ARG, "non-finite antenna position");
+
+  epic::ImageKernelShape shape{};
+  if (!epic::image_kernel_shape(d->grid_n, &shape))
+    return fail(EPIC_ERR_UNSUPPORTED, "grid_n must be 16, 32, 64 or 128 in this build");
+  if (d->n_ant > shape.max_ant)
+    return fail(EPIC_ERR_UNSUPPORTED, "n_ant exceeds " + std::to_string(shape.max_ant) +
+                                          " for this grid size");
+
+  epic_plan_s* p = new (std::nothrow) epic_plan_s();
+  if (!p) return fail(EPIC_ERR_OOM, "host allocation failed");
+  p->na = d->n_ant;
+  p->nc = d->n_chan;
+  p->n = d->grid_n;
+  p->k = d->kernel_support;
+  p->kernel = d->kernel;
+  p->kparam = d->kernel_param;
+  p->cell = d->cell_wavelengths;
+  p->input = d->input;
+  p->ant.assign(d->ant_xy_m, d->ant_xy_m + 2 * d->n_ant);
+  p->freq.assign(d->freq_hz, d->freq_hz + d->n_chan);
+  p->vscale.assign(d->n_chan, 1.0f);
+  if (d->voltage_scale) p->vscale.assign(d->voltage_scale, d->voltage_scale + d->n_chan);
+  p->flags.assign(d->n_ant, 0);
+  if (d->flags)
+    for (int a = 0; a < d->n_ant; ++a) p->flags[a] = d->flags[a] ? 1 : 0;
+  p->stream = static_cast<cudaStream_t>(d->cuda_stream);
+  p->shape = shape;
+
+  // ---- gridding tables (Eq. 9), FP64 ----
+  const int Na = p->na, C = p->nc, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
+  p->base.assign(static_cast<size_t>(C) * Na * 2, 0);
+  p->w64.assign(static_cast<size_t>(C) * Na * KK, 0.0);
+  p->y0.assign(C, 0);
+  p->rows.assign(C, 0);
+  std::vector<int> cell0(static_cast<size_t>(C) * Na, -1);
+  std::vector<float> wts(static_cast<size_t>(C) * Na * KK, 0.0f);
+  int n_unflagged = 0;
+  for (int a = 0; a < Na; ++a) n_unflagged += p->flags[a] ? 0 : 1;
+  if (n_unflagged == 0) {
+    delete p;
+    return fail(EPIC_ERR_INVALID_ARG, "every antenna is flagged");
+  }
+  for (int c = 0; c < C; ++c) {
+    const double f = p->freq[c];
+    int ymin = N, ymax = -1;
+    for (int a = 0; a < Na; ++a) {
+      const double ux = (p->ant[2 * a] * f) / kC;
+      const double uy = (p->ant[2 * a + 1] * f) / kC;
+      const double px = ux / p->cell + N / 2;
+      const double py = uy / p->cell + N / 2;
+      const double bxd = std::floor(px + 0.5), byd = std::floor(py + 0.5);
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      if (!(std::fabs(bxd) < 1e9 && std::fabs(byd) < 1e9)) {
+        if (p->flags[a]) continue;
+        delete p;
+        return fail(EPIC_ERR_GRID_TOO_SMALL, "antenna far outside the grid");
+      }
+      const int bx = static_cast<int>(bxd), by = static_cast<int>(byd);
+      p->base[ob] = bx;
+      p->base[ob + 1] = by;
+      if (p->flags[a]) continue;
+      if (bx - h < 0 || bx + h >= N || by - h < 0 || by + h >= N) {
+        delete p;
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "antenna %d channel %d: stencil outside the %dx%d grid", a, c, N, N);
+        return fail(EPIC_ERR_GRID_TOO_SMALL, msg);
+      }
+      double* w = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
+      double sum = 0.0;
+      const double half = (p->kparam * f / kC) / p->cell / 2.0;
+      for (int dy = 0; dy < K; ++dy)
+        for (int dx = 0; dx < K; ++dx) {
+          const int jx = bx + dx - h, jy = by + dy - h;
+          double v;
+          if (p->kernel == EPIC_KERNEL_GAUSSIAN) {
+            const double ex = jx - px, ey = jy - py;
+            const double d2 = ex * ex + ey * ey;
+            v = std::exp(-d2 / (2.0 * p->kparam * p->kparam));
+          } else {
+            v = (std::fabs(jx - px) <= half && std::fabs(jy - py) <= half) ? 1.0 : 0.0;
+          }
+          w[dy * K + dx] = v;
+          sum += v;
+        }
+      if (!(sum > 0)) {
+        delete p;
+        return fail(EPIC_ERR_INVALID_ARG, "gridding kernel has no support for antenna " + std::to_string(a));
+      }
+      for (int i = 0; i < KK; ++i) w[i] /= sum;
+      ymin = std::min(ymin, by - h);
+      ymax = std::max(ymax, by + h);
+    }
+    p->y0[c] = ymin;
+    p->rows[c] = ymax - ymin + 1;
+    p->rows_alloc = std::max(p->rows_alloc, p->rows[c]);
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      const int bx = p->base[ob], by = p->base[ob + 1];
+      cell0[static_cast<size_t>(c) * Na + a] = (by - h - ymin) * N + (bx - h);
+      const double* w = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
+      float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
+      for (int dy = 0; dy < K; ++dy)
+        for (int dx = 0; dx < K; ++dx) {
+          const int jx = bx + dx - h, jy = by + dy - h;
+          const double sgn = ((jx + jy) & 1) ? -1.0 : 1.0;   // centring of Eq. 10
+          wf[dy * K + dx] = static_cast<float>(w[dy * K + dx] * sgn / Na);
+        }
+    }
+  }
+
+  // ---- launch shape ----
+  p->rs = epic::image_rs(p->rows_alloc);
+  p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  p->device = dev;
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (p->smem > static_cast<size_t>(smem_optin)) {
+    const std::string msg = "array footprint needs " + std::to_string(p->smem) +
+                            " B of shared memory (limit " + std::to_string(smem_optin) + ")";
+    delete p;
+    return fail(EPIC_ERR_UNSUPPORTED, msg);
+  }
+  int per_sm = 0;
+  e = epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
+  if (e != cudaSuccess || per_sm < 1) {
+    delete p;
+    return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
+                            : fail(EPIC_ERR_UNSUPPORTED, "image kernel cannot be resident");
+  }
+  p->ctas = per_sm * p->sms;
+
+  // ---- device tables ----
+  std::vector<float2> twid(N);
+  for (int m = 0; m < N; ++m)
+    twid[m] = make_float2(static_cast<float>(std::cos(2.0 * kPi * m / N)),
+                          static_cast<float>(std::sin(2.0 * kPi * m / N)));
+  std::vector<int2> win(C);
+  for (int c = 0; c < C; ++c) win[c] = make_int2(p->y0[c], p->rows[c]);
+  std::vector<double2> gain(static_cast<size_t>(C) * Na, make_double2(1.0, 0.0));
+  std::vector<float2> wgain(static_cast<size_t>(C) * Na, make_float2(1.0f, 0.0f));
+
+  auto up = [&](auto& buf, const auto& host) -> cudaError_t {
+    cudaError_t e2 = buf.alloc(host.size());
+    if (e2 != cudaSuccess) return e2;
+    return cudaMemcpy(buf.p, host.data(), host.size() * sizeof(host[0]), cudaMemcpyHostToDevice);
+  };
+  cudaError_t es[] = {up(p->d_cell0, cell0), up(p->d_wts, wts), up(p->d_wgain, wgain),
+                      up(p->d_gain, gain), up(p->d_vscale, p->vscale), up(p->d_win, win),
+                      up(p->d_twid, twid), up(p->d_flags, p->flags)};
+  for (cudaError_t x : es)
+    if (x != cudaSuccess) {
+      epic_plan_destroy(p);
+      return x == cudaErrorMemoryAllocation ? fail(EPIC_ERR_OOM, "device allocation failed")
+                                            : cuda_fail(x, "table upload");
+    }
+  e = p->d_held.alloc(1);
+  if (e == cudaSuccess) e = cudaMemset(p->d_held.p, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    epic_plan_destroy(p);
+    return cuda_fail(e, "counter");
+  }
+  *out = p;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_destroy(epic_plan_t p) {
+  if (!p) return EPIC_OK;
+  cudaStreamSynchronize(p->stream);
+  p->d_cell0.release();
+  p->d_wts.release();
+  p->d_wgain.release();
+  p->d_gain.release();
+  p->d_vscale.release();
+  p->d_win.release();
+  p->d_twid.release();
+  p->d_flags.release();
+  p->d_a0.release();
+  p->d_dden.release();
+  p->d_kacc.release();
+  p->d_pacc.release();
+  p->d_held.release();
+  p->d_stage_in.release();
+  p->d_stage_img.release();
+  delete p;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_set_stream(epic_plan_t p, void* stream) {
+  if (epic_status s = check_plan(p)) return s;
+  p->stream = static_cast<cudaStream_t>(stream);
+  return EPIC_OK;
+}
+
+epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!info) return fail(EPIC_ERR_INVALID_ARG, "info is NULL");
+  info->n_ant = p->na;
+  info->n_chan = p->nc;
+  info->grid_n = p->n;
+  info->kernel_support = p->k;
+  info->window_rows = p->rows_alloc;
+  info->cal_kx = p->cal ? p->k0x : -1;
+  info->cal_ky = p->cal ? p->k0y : -1;
+  info->ctas = p->ctas;
+  info->units_per_chan = 0;
+  info->smem_bytes = p->smem;
+  info->frames_pending = p->frames;
+  info->iteration = p->iteration;
+  return EPIC_OK;
+}
+
+epic_status epic_set_gains(epic_plan_t p, const double* gains) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!gains) return fail(EPIC_ERR_INVALID_ARG, "gains is NULL");
+  const size_t n = static_cast<size_t>(p->nc) * p->na;
+  std::vector<double2> g(n);
+  std::vector<float2> w(n);
+  for (size_t i = 0; i < n; ++i) {
+    const double re = gains[2 * i], im = gains[2 * i + 1];
+    const double m2 = re * re + im * im;
+    if (!std::isfinite(re) || !std::isfinite(im) || !(m2 > 0))
+      return fail(EPIC_ERR_INVALID_ARG, "gains must be finite and non-zero");
+    g[i] = make_double2(re, im);
+    w[i] = make_float2(static_cast<float>(re / m2), static_cast<float>(-im / m2));
+  }
+  EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  return EPIC_OK;
+}
+
+epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
+                       int accumulate) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_volt || !d_image) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
+  if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
+  const size_t img_bytes = static_cast<size_t>(p->nc) * p->n * p->n * sizeof(double);
+  if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_image, 0, img_bytes, p->stream));
+  epic::ImageArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.cell0 = p->d_cell0.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win = p->d_win.p;
+  a.twid = p->d_twid.p;
+  a.image = d_image;
+  a.img_scale = 1.0 / static_cast<double>(n_time);
+  a.do_cal = p->cal ? 1 : 0;
+  a.k0x = p->cal ? p->k0x : 0;
+  a.k0y = p->cal ? p->k0y : 0;
+  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
+  a.kacc = p->d_kacc.p;
+  a.pacc = p->d_pacc.p;
+  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.rows_alloc = p->rows_alloc;
+  a.rs = p->rs;
+  const long long units = static_cast<long long>(p->nc) * a.segs;
+  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
+  a.smem = p->smem;
+  EPIC_CUDA(epic::launch_image(p->n, a, p->stream));
+  if (p->cal) p->frames += n_time;
+  return EPIC_OK;
+}
+
+epic_status epic_image_host(epic_plan_t p, const void* h_volt, long long n_time, double* h_image,
+                            int accumulate) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!h_volt || !h_image) return fail(EPIC_ERR_INVALID_ARG, "NULL host buffer");
+  if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
+  const size_t elem = p->input == EPIC_IN_CI4 ? 1 : 8;
+  const size_t in_bytes = static_cast<size_t>(n_time) * p->nc * p->na * elem;
+  const size_t img_n = static_cast<size_t>(p->nc) * p->n * p->n;
+  if (p->d_stage_in.n < in_bytes) {
+    cudaError_t e = p->d_stage_in.alloc(in_bytes);
+    if (e != cudaSuccess) return fail(EPIC_ERR_OOM, "staging allocation failed");
+  }
+  if (p->d_stage_img.n < img_n) {
+    cudaError_t e = p->d_stage_img.alloc(img_n);
+    if (e != cudaSuccess) return fail(EPIC_ERR_OOM, "staging allocation failed");
+  }
+  EPIC_CUDA(cudaMemcpyAsync(p->d_stage_in.p, h_volt, in_bytes, cudaMemcpyHostToDevice, p->stream));
+  if (accumulate)
+    EPIC_CUDA(cudaMemcpyAsync(p->d_stage_img.p, h_image, img_n * sizeof(double),
+                              cudaMemcpyHostToDevice, p->stream));
+  if (epic_status s = epic_image(p, p->d_stage_in.p, n_time, p->d_stage_img.p, accumulate)) return s;
+  EPIC_CUDA(cudaMemcpyAsync(h_image, p->d_stage_img.p, img_n * sizeof(double), cudaMemcpyDeviceToHost,
+                            p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  return EPIC_OK;
+}
+
+epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_src,
+                             const double* src, double gamma, const double* g0) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!(gamma >= 0.0 && gamma < 1.0)) return fail(EPIC_ERR_INVALID_ARG, "gamma must be in [0, 1)");
+  if (n_src < 1 || !src) return fail(EPIC_ERR_INVALID_ARG, "at least one model source is required");
+  const int Na = p->na, C = p->nc, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
+  // nearest pixel centre: l = (k - N/2) / (N du)
+  const double kxd = std::floor(cal_l * N * p->cell + N / 2 + 0.5);
+  const double kyd = std::floor(cal_m * N * p->cell + N / 2 + 0.5);
+  if (!(kxd >= 0 && kxd < N && kyd >= 0 && kyd < N))
+    return fail(EPIC_ERR_INVALID_ARG, "calibrator outside the image");
+  const int k0x = static_cast<int>(kxd), k0y = static_cast<int>(kyd);
+  const size_t n = static_cast<size_t>(C) * Na;
+  std::vector<double2> a0(n), dd(n), g(n);
+  std::vector<float2> w(n);
+  for (int c = 0; c < C; ++c) {
+    const double f = p->freq[c];
+    std::vector<std::complex<double>> A(Na, 0.0);
+    // A_{0,a}: exact response of pixel k0 to antenna a through the stencil
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      const int bx = p->base[ob], by = p->base[ob + 1];
+      const double* wa = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
+      std::complex<double> s = 0.0;
+      for (int dy = 0; dy < K; ++dy)
+        for (int dx = 0; dx < K; ++dx) {
+          const int jx = bx + dx - h, jy = by + dy - h;
+          long long m = static_cast<long long>(jx - N / 2) * (k0x - N / 2) +
+                        static_cast<long long>(jy - N / 2) * (k0y - N / 2);
+          m %= N;
+          if (m < 0) m += N;
+          const double ph = 2.0 * kPi * static_cast<double>(m) / N;
+          s += wa[dy * K + dx] * std::complex<double>(std::cos(ph), std::sin(ph));
+        }
+      A[a] = s / static_cast<double>(Na);
+    }
+    // D_a = sum_{b != a, unflagged} conj(A_b) V^M_ab with V^M from point
+    // sources: sum_s S_s e^{-2 pi i u_a.s} (B_s - conj(A_a) e^{+2 pi i u_a.s}),
+    // B_s = sum_b conj(A_b) e^{+2 pi i u_b.s}.
+    std::vector<std::complex<double>> D(Na, 0.0);
+    for (int si = 0; si < n_src; ++si) {
+      const double l = src[3 * si], m = src[3 * si + 1], S = src[3 * si + 2];
+      std::vector<std::complex<double>> ph(Na);
+      std::complex<double> B = 0.0;
+      for (int b = 0; b < Na; ++b) {
+        const double ux = (p->ant[2 * b] * f) / kC, uy = (p->ant[2 * b + 1] * f) / kC;
+        const double arg = 2.0 * kPi * (ux * l + uy * m);
+        ph[b] = std::complex<double>(std::cos(arg), std::sin(arg));  // e^{+2 pi i u_b.s}
+        if (!p->flags[b]) B += std::conj(A[b]) * ph[b];
+      }
+      for (int a = 0; a < Na; ++a) D[a] += S * (std::conj(ph[a]) * B - std::conj(A[a]));
+    }
+    for (int a = 0; a < Na; ++a) {
+      const size_t i = static_cast<size_t>(c) * Na + a;
+      a0[i] = make_double2(A[a].real(), A[a].imag());
+      dd[i] = make_double2(D[a].real(), D[a].imag());
+      double gr = 1.0, gi = 0.0;
+      if (g0) {
+        gr = g0[2 * i];
+        gi = g0[2 * i + 1];
+        if (!std::isfinite(gr) || !std::isfinite(gi) || !(gr * gr + gi * gi > 0))
+          return fail(EPIC_ERR_INVALID_ARG, "initial gains must be finite and non-zero");
+      }
+      g[i] = make_double2(gr, gi);
+      const double m2 = gr * gr + gi * gi;
+      w[i] = make_float2(static_cast<float>(gr / m2), static_cast<float>(-gi / m2));
+    }
+  }
+  if (!p->d_a0.p) {
+    cudaError_t es[] = {p->d_a0.alloc(n), p->d_dden.alloc(n), p->d_kacc.alloc(n), p->d_pacc.alloc(n)};
+    for (cudaError_t x : es)
+      if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "EPICal allocation failed");
+  }
+  EPIC_CUDA(cudaMemcpyAsync(p->d_a0.p, a0.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_dden.p, dd.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemsetAsync(p->d_kacc.p, 0, n * sizeof(double2), p->stream));
+  EPIC_CUDA(cudaMemsetAsync(p->d_pacc.p, 0, n * sizeof(double), p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  p->k0x = k0x;
+  p->k0y = k0y;
+  p->gamma = gamma;
+  p->cal = true;
+  p->frames = 0;
+  p->iteration = 0;
+  return EPIC_OK;
+}
+
+epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!p->cal) return fail(EPIC_ERR_STATE, "EPICal is not configured");
+  if (p->frames < 1) return fail(EPIC_ERR_STATE, "no frames imaged since the last update");
+  epic::UpdateArgs u{};
+  u.n_chan = p->nc;
+  u.n_ant = p->na;
+  u.kacc = p->d_kacc.p;
+  u.pacc = p->d_pacc.p;
+  u.inv_frames = 1.0 / static_cast<double>(p->frames);
+  u.a0 = p->d_a0.p;
+  u.dden = p->d_dden.p;
+  u.gain = p->d_gain.p;
+  u.wgain = p->d_wgain.p;
+  u.flags = p->d_flags.p;
+  u.gamma = p->gamma;
+  u.dmin = kDmin;
+  u.gout = reinterpret_cast<double2*>(d_gains_out);
+  u.status = d_status;
+  u.held_count = p->d_held.p;
+  EPIC_CUDA(epic::launch_update(u, p->stream));
+  p->frames = 0;
+  p->iteration += 1;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_sync(epic_plan_t p, int* n_held) {
+  if (epic_status s = check_plan(p)) return s;
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  int held = 0;
+  EPIC_CUDA(cudaMemcpy(&held, p->d_held.p, sizeof(int), cudaMemcpyDeviceToHost));
+  EPIC_CUDA(cudaMemset(p->d_held.p, 0, sizeof(int)));
+  if (n_held) *n_held = held;
+  if (held > 0) return fail(EPIC_ERR_NUMERIC, std::to_string(held) + " gains held by the EPICal update");
+  return EPIC_OK;
+}
+
+epic_status epical_get_gains(epic_plan_t p, double* h_gains) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!h_gains) return fail(EPIC_ERR_INVALID_ARG, "NULL output");
+  const size_t n = static_cast<size_t>(p->nc) * p->na;
+  EPIC_CUDA(cudaMemcpyAsync(h_gains, p->d_gain.p, n * sizeof(double2), cudaMemcpyDeviceToHost, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  return EPIC_OK;
+}
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int n_chan, n_ant, cal, k0x, k0y, pad;
+  double gamma;
+  long long frames, iteration;
+};
+}  // namespace
+
+epic_status epical_get_state(epic_plan_t p, void* buf, size_t* bytes) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!bytes) return fail(EPIC_ERR_INVALID_ARG, "bytes is NULL");
+  const size_t n = static_cast<size_t>(p->nc) * p->na;
+  const size_t need = sizeof(StateHeader) + n * (sizeof(double2) * 2 + sizeof(double));
+  if (!buf) {
+    *bytes = need;
+    return EPIC_OK;
+  }
+  if (*bytes < need) return fail(EPIC_ERR_INVALID_ARG, "state buffer too small");
+  if (!p->cal) return fail(EPIC_ERR_STATE, "EPICal is not configured");
+  StateHeader hd{};
+  std::memcpy(hd.magic, "EPICST1", 8);
+  hd.n_chan = p->nc;
+  hd.n_ant = p->na;
+  hd.cal = 1;
+  hd.k0x = p->k0x;
+  hd.k0y = p->k0y;
+  hd.gamma = p->gamma;
+  hd.frames = p->frames;
+  hd.iteration = p->iteration;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  std::memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  EPIC_CUDA(cudaMemcpyAsync(o, p->d_gain.p, n * sizeof(double2), cudaMemcpyDeviceToHost, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(o + n * sizeof(double2), p->d_kacc.p, n * sizeof(double2),
+                            cudaMemcpyDeviceToHost, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(o + 2 * n * sizeof(double2), p->d_pacc.p, n * sizeof(double),
+                            cudaMemcpyDeviceToHost, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  *bytes = need;
+  return EPIC_OK;
+}
+
+epic_status epical_set_state(epic_plan_t p, const void* buf, size_t bytes) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!buf) return fail(EPIC_ERR_INVALID_ARG, "NULL state");
+  if (!p->cal) return fail(EPIC_ERR_STATE, "configure EPICal before restoring its state");
+  const size_t n = static_cast<size_t>(p->nc) * p->na;
+  const size_t need = sizeof(StateHeader) + n * (sizeof(double2) * 2 + sizeof(double));
+  if (bytes != need) return fail(EPIC_ERR_INVALID_ARG, "state size mismatch");
+  StateHeader hd{};
+  std::memcpy(&hd, buf, sizeof hd);
+  if (std::memcmp(hd.magic, "EPICST1", 8) != 0 || hd.n_chan != p->nc || hd.n_ant != p->na)
+    return fail(EPIC_ERR_INVALID_ARG, "state header does not match this plan");
+  const unsigned char* i = static_cast<const unsigned char*>(buf) + sizeof hd;
+  std::vector<double2> g(n);
+  std::memcpy(g.data(), i, n * sizeof(double2));
+  std::vector<float2> w(n);
+  for (size_t k = 0; k < n; ++k) {
+    const double m2 = g[k].x * g[k].x + g[k].y * g[k].y;
+    w[k] = make_float2(static_cast<float>(g[k].x / m2), static_cast<float>(-g[k].y / m2));
+  }
+  EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_kacc.p, i + n * sizeof(double2), n * sizeof(double2),
+                            cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_pacc.p, i + 2 * n * sizeof(double2), n * sizeof(double),
+                            cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  p->k0x = hd.k0x;
+  p->k0y = hd.k0y;
+  p->gamma = hd.gamma;
+  p->frames = hd.frames;
+  p->iteration = hd.iteration;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_get_grid_table(epic_plan_t p, int* base_xy, double* w) {
+  if (epic_status s = check_plan(p)) return s;
+  if (base_xy) std::memcpy(base_xy, p->base.data(), p->base.size() * sizeof(int));
+  if (w) std::memcpy(w, p->w64.data(), p->w64.size() * sizeof(double));
+  return EPIC_OK;
+}
+
+epic_status epic_unpack_ci4(epic_plan_t p, const unsigned char* d_in, float* d_out, long long n) {
+  if (epic_status s = check_plan(p)) return s;
+  if (n < 0 || (n > 0 && (!d_in || !d_out))) return fail(EPIC_ERR_INVALID_ARG, "bad unpack arguments");
+  EPIC_CUDA(epic::launch_unpack(d_in, reinterpret_cast<float2*>(d_out), n, p->stream));
+  return EPIC_OK;
+}
+
+}  // extern "C"
