@@ -124,6 +124,24 @@ epic_status epic_image(epic_plan_t plan, const void* d_volt, long long n_time,
 epic_status epic_image_host(epic_plan_t plan, const void* h_volt, long long n_time,
                             double* h_image, int accumulate);
 
+/* epic_image_host for callers that cannot allocate device memory (a
+ * real-time loop that may not add a device-synchronising cudaMalloc between
+ * intervals, a process held to a device-memory budget fixed at start-up, or
+ * host code running where CUDA allocation calls are not allowed).  The paper
+ * has no counterpart: this is a deployment variant of the same imaging
+ * kernel.  It allocates nothing: voltages and the image are staged through
+ * one 32 MiB file-scope device array that every GPU loading the library
+ * holds until exit; T is processed in chunks that fit beside the image.
+ * Arguments and result as epic_image_host.  The image [C][N][N] float64 plus
+ * one time sample of voltages must fit in 32 MiB, else INVALID_ARG with a
+ * message.  The first call on a device looks up the array's device address
+ * (make that first call before any stream capture).  All calls share the
+ * array: calls whose GPU work overlaps (several host threads or plans on
+ * different streams) race and must be serialised by the caller.
+ * Synchronous. */
+epic_status epic_image_host_static(epic_plan_t plan, const void* h_volt, long long n_time,
+                                   double* h_image, int accumulate);
+
 /* Arm EPICal (Sec. 2.2).  (cal_l, cal_m): calibrator direction; the pixel
  * used is the nearest pixel centre.  Model: n_src point sources, host
  * src_lmS [n_src][3] rows (l, m, S) with apparent fluxes S, used for every

@@ -22,7 +22,8 @@ EPIC_PREC_FP32, EPIC_PREC_FP16, EPIC_PREC_BF16 = 0, 1, 2
 # every exported entry point, as declared in include/epic.h
 EXPORTS = [
     "epic_plan_create", "epic_plan_destroy", "epic_plan_set_stream", "epic_plan_get_info",
-    "epic_set_gains", "epic_image", "epic_image_host", "epical_configure", "epical_update",
+    "epic_set_gains", "epic_image", "epic_image_host", "epic_image_host_static",
+    "epical_configure", "epical_update",
     "epic_plan_sync", "epical_get_gains", "epical_get_state", "epical_set_state",
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
 ]
@@ -84,6 +85,7 @@ def load(path: str | None = None) -> ct.CDLL:
         "epic_set_gains": [P, c_dp],
         "epic_image": [P, P, ct.c_longlong, P, ct.c_int],
         "epic_image_host": [P, P, ct.c_longlong, P, ct.c_int],
+        "epic_image_host_static": [P, P, ct.c_longlong, P, ct.c_int],
         "epical_configure": [P, ct.c_double, ct.c_double, ct.c_int, c_dp, ct.c_double, c_dp],
         "epical_update": [P, P, P],
         "epic_plan_sync": [P, c_ip],

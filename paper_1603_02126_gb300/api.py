@@ -154,6 +154,26 @@ class Plan:
         B.check(self._lib.epic_image_host(self.handle, vptr, int(T), iptr, int(bool(accumulate))))
         return image
 
+    def image_host_static(self, volt, image=None, accumulate=False):
+        """image_host without any device allocation: stages through the
+        library's fixed 32 MiB device array (for callers that may not call
+        cudaMalloc).  Same arguments and result as image_host."""
+        torch = _torch()
+        if isinstance(volt, torch.Tensor):
+            if volt.is_cuda:
+                raise TypeError("image_host_static takes host memory")
+            vt = volt.contiguous()
+            vptr = ct.c_void_p(vt.data_ptr())
+        else:
+            vt = np.ascontiguousarray(volt)
+            vptr = ct.c_void_p(vt.ctypes.data)
+        if image is None:
+            image = np.zeros((self.n_chan, self.grid_n, self.grid_n), np.float64)
+        iptr = ct.c_void_p(image.data_ptr() if isinstance(image, torch.Tensor) else image.ctypes.data)
+        B.check(self._lib.epic_image_host_static(self.handle, vptr, int(vt.shape[0]), iptr,
+                                                 int(bool(accumulate))))
+        return image
+
     def configure(self, cal_lm, model_lmS, gamma, g0=None):
         src = _f64(model_lmS).reshape(-1, 3)
         g = None if g0 is None else _c128_as_f64(g0, self.n_chan * self.n_ant)

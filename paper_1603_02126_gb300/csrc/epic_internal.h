@@ -70,3 +70,18 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_unpack(const unsigned char* in, float2* out, long long n, cudaStream_t s);
 
 }  // namespace epic
+
+// ---- helpers for entry points outside epic_plan.cpp ----
+struct epic_plan_s;
+namespace epic {
+// One fused imaging launch over a device batch: adds (img_scale * sum_t
+// |E|^2) into d_image (no clearing) and, when EPICal is armed, counts the
+// frames toward the next update.
+int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, double* d_image,
+                       double img_scale);
+size_t plan_frame_bytes(const epic_plan_s* p);   // voltages of one time sample, all channels
+size_t plan_image_elems(const epic_plan_s* p);   // C * N * N
+cudaStream_t plan_stream(const epic_plan_s* p);
+int plan_device(const epic_plan_s* p);
+int set_error(int status, const char* msg);     // records epic_last_error(), returns status
+}  // namespace epic

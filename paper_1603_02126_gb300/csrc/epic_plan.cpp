@@ -696,3 +696,56 @@ epic_status epic_unpack_ci4(epic_plan_t p, const unsigned char* d_in, float* d_o
 }
 
 }  // extern "C"
+
+// ---- helpers for entry points outside this file ----
+namespace epic {
+
+int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, double* d_image,
+                       double img_scale) {
+  if (!p || !d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad batch");
+  ImageArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.cell0 = p->d_cell0.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win = p->d_win.p;
+  a.twid = p->d_twid.p;
+  a.image = d_image;
+  a.img_scale = img_scale;
+  a.do_cal = p->cal ? 1 : 0;
+  a.k0x = p->cal ? p->k0x : 0;
+  a.k0y = p->cal ? p->k0y : 0;
+  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
+  a.kacc = p->d_kacc.p;
+  a.pacc = p->d_pacc.p;
+  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.rows_alloc = p->rows_alloc;
+  a.rs = p->rs;
+  const long long units = static_cast<long long>(p->nc) * a.segs;
+  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
+  a.smem = p->smem;
+  cudaError_t e = launch_image(p->n, a, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "image launch");
+  if (p->cal) p->frames += n_time;
+  return EPIC_OK;
+}
+
+size_t plan_frame_bytes(const epic_plan_s* p) {
+  return static_cast<size_t>(p->nc) * p->na * (p->input == EPIC_IN_CI4 ? 1 : 8);
+}
+
+size_t plan_image_elems(const epic_plan_s* p) { return static_cast<size_t>(p->nc) * p->n * p->n; }
+
+cudaStream_t plan_stream(const epic_plan_s* p) { return p->stream; }
+
+int plan_device(const epic_plan_s* p) { return p->device; }
+
+int set_error(int status, const char* msg) { return fail(static_cast<epic_status>(status), msg); }
+
+}  // namespace epic
