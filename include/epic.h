@@ -52,6 +52,11 @@ typedef enum {
 typedef enum { EPIC_KERNEL_GAUSSIAN = 0, EPIC_KERNEL_TOPHAT = 1 } epic_kernel_type;
 typedef enum { EPIC_IN_CI4 = 0, EPIC_IN_COMPLEX64 = 1 } epic_input_format;
 typedef enum { EPIC_PREC_FP32 = 0, EPIC_PREC_FP16 = 1, EPIC_PREC_BF16 = 2 } epic_precision;
+/* Kernel structure of epic_image.  FUSED: one persistent launch keeps each
+ * frame in one SM (N <= 128).  UNFUSED: the plain path, grid and row
+ * spectra pass through device memory in batches (N = 32..512).  AUTO picks
+ * FUSED when it applies. */
+typedef enum { EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2 } epic_path;
 
 /* Plan description (Sec. 2.1: antenna positions, grid, kernel, channels). */
 typedef struct {
@@ -59,7 +64,7 @@ typedef struct {
   const double* ant_xy_m;      /* host [Na][2]: planar East, North positions, metres */
   int n_chan;                  /* C >= 1 */
   const double* freq_hz;       /* host [C]: channel centre frequencies */
-  int grid_n;                  /* N: power of two, 16..128 */
+  int grid_n;                  /* N: power of two, 16..128 (FUSED), 32..512 (UNFUSED) */
   double cell_wavelengths;     /* grid cell du in wavelengths (0.5 = full sky) */
   int kernel;                  /* epic_kernel_type: antenna illumination W_a */
   int kernel_support;          /* K: odd stencil side in cells, 1..7 */
@@ -69,6 +74,8 @@ typedef struct {
   const unsigned char* flags;  /* host [Na], 1 = antenna flagged, or NULL */
   int precision;               /* epic_precision of the FFT; FP32 only here */
   void* cuda_stream;           /* cudaStream_t for all work; NULL = default */
+  int path;                    /* epic_path */
+  size_t workspace_bytes;      /* UNFUSED batch scratch budget; 0 = 2 GiB */
 } epic_plan_desc;
 
 /* Read-only facts about a plan (epic_plan_get_info). */
@@ -81,6 +88,8 @@ typedef struct {
   size_t smem_bytes;           /* dynamic shared memory of the image kernel */
   long long frames_pending;    /* frames correlated since the last update */
   long long iteration;         /* completed EPICal updates */
+  int path;                    /* epic_path in use (FUSED or UNFUSED) */
+  int batch_time;              /* UNFUSED: time samples per batch (0 before use) */
 } epic_plan_info;
 
 /* Build the gridding tables of Eq. 9 for every (channel, antenna): the
@@ -134,7 +143,8 @@ epic_status epic_image_host(epic_plan_t plan, const void* h_volt, long long n_ti
  * holds until exit; T is processed in chunks that fit beside the image.
  * Arguments and result as epic_image_host.  The image [C][N][N] float64 plus
  * one time sample of voltages must fit in 32 MiB, else INVALID_ARG with a
- * message.  The first call on a device looks up the array's device address
+ * message; a plan on the UNFUSED path gives UNSUPPORTED (that path needs its
+ * own scratch).  The first call on a device looks up the array's device address
  * (make that first call before any stream capture).  All calls share the
  * array: calls whose GPU work overlaps (several host threads or plans on
  * different streams) race and must be serialised by the caller.

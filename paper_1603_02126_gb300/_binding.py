@@ -18,6 +18,7 @@ STATUS_NAMES = {
 EPIC_KERNEL_GAUSSIAN, EPIC_KERNEL_TOPHAT = 0, 1
 EPIC_IN_CI4, EPIC_IN_COMPLEX64 = 0, 1
 EPIC_PREC_FP32, EPIC_PREC_FP16, EPIC_PREC_BF16 = 0, 1, 2
+EPIC_PATH_AUTO, EPIC_PATH_FUSED, EPIC_PATH_UNFUSED = 0, 1, 2
 
 # every exported entry point, as declared in include/epic.h
 EXPORTS = [
@@ -44,6 +45,8 @@ class PlanDesc(ct.Structure):
         ("flags", c_u8p),
         ("precision", ct.c_int),
         ("cuda_stream", ct.c_void_p),
+        ("path", ct.c_int),
+        ("workspace_bytes", ct.c_size_t),
     ]
 
 
@@ -54,6 +57,7 @@ class PlanInfo(ct.Structure):
         ("cal_kx", ct.c_int), ("cal_ky", ct.c_int), ("ctas", ct.c_int),
         ("units_per_chan", ct.c_int), ("smem_bytes", ct.c_size_t),
         ("frames_pending", ct.c_longlong), ("iteration", ct.c_longlong),
+        ("path", ct.c_int), ("batch_time", ct.c_int),
     ]
 
 

@@ -16,6 +16,7 @@ from ._binding import EpicError  # noqa: F401
 
 _KERNELS = {"gaussian": B.EPIC_KERNEL_GAUSSIAN, "tophat": B.EPIC_KERNEL_TOPHAT}
 _INPUTS = {"ci4": B.EPIC_IN_CI4, "c64": B.EPIC_IN_COMPLEX64}
+_PATHS = {"auto": B.EPIC_PATH_AUTO, "fused": B.EPIC_PATH_FUSED, "unfused": B.EPIC_PATH_UNFUSED}
 
 
 def _torch():
@@ -55,7 +56,8 @@ class Plan:
     """One EPIC/EPICal plan: array, grid, kernel and channels (Sec. 2.1)."""
 
     def __init__(self, ant_xy_m, freq_hz, grid_n, cell=0.5, kernel="gaussian", support=3,
-                 param=0.5, input="ci4", voltage_scale=None, flags=None, stream=None):
+                 param=0.5, input="ci4", voltage_scale=None, flags=None, stream=None,
+                 path="auto", workspace_bytes=0):
         lib = B.load()
         self._lib = lib
         self.ant = _f64(ant_xy_m).reshape(-1, 2)
@@ -82,6 +84,8 @@ class Plan:
         d.flags = None if self._fl is None else self._fl.ctypes.data_as(B.c_u8p)
         d.precision = B.EPIC_PREC_FP32
         d.cuda_stream = ct.c_void_p(int(stream))
+        d.path = _PATHS[path]
+        d.workspace_bytes = int(workspace_bytes)
         h = ct.c_void_p()
         B.check(lib.epic_plan_create(ct.byref(h), ct.byref(d)))
         self.handle = h

@@ -69,6 +69,32 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 
 cudaError_t launch_unpack(const unsigned char* in, float2* out, long long n, cudaStream_t s);
 
+// Arguments of one batch of the plain unfused path (epic_unfused.cu).
+struct UnfusedArgs {
+  const void* volt;        // device [T][C][Na] (whole call; batches index into it)
+  int input_fmt;
+  int n_chan, n_ant, support, grid_n;
+  const int* cell0;        // [C][Na] window cell of tap (0,0); -1 = flagged
+  const float* wts;        // [C][Na][K*K] folded weights
+  const float2* wgain;     // [C][Na] 1/g
+  const float* vscale;     // [C] or nullptr
+  const int2* win;         // [C] (y0, rows)
+  const float2* twid;      // [N]
+  float2* grid;            // scratch [nt*C][rows_alloc][N]
+  float2* spec;            // scratch [nt*C][N][rs] transposed row spectra
+  float2* pix;             // scratch [nt*C] calibrator pixel per frame
+  int rows_alloc, rs;
+  double* image;           // [C][N][N]
+  double img_scale;
+  int do_cal, k0x, k0y;
+  float pix_sign;
+  double2* kacc;
+  double* pacc;
+};
+bool unfused_supported(int n);
+// Enqueue the four kernels of one batch of nt time samples starting at t0.
+cudaError_t launch_unfused_batch(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
+
 }  // namespace epic
 
 // ---- helpers for entry points outside epic_plan.cpp ----

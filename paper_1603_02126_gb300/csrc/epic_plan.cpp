@@ -109,6 +109,12 @@ struct epic_plan_s {
   // host-API staging
   DevBuf<unsigned char> d_stage_in;
   DevBuf<double> d_stage_img;
+
+  // path and unfused scratch
+  int path = EPIC_PATH_FUSED;
+  size_t workspace_budget = static_cast<size_t>(2) << 30;
+  DevBuf<float2> d_ws;          // [nt*C] x (rows_alloc*N + N*rs + 1)
+  int ws_time = 0;              // time samples the scratch holds
 };
 
 namespace {
@@ -131,6 +137,61 @@ int choose_segments(int n_chan, long long n_time, int ctas) {
     if (units >= 16LL * ctas) return static_cast<int>(s);
   }
   return static_cast<int>(best);
+}
+
+// Plain unfused path: batches of time samples through the device scratch.
+epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, double* d_image) {
+  const int C = p->nc, N = p->n;
+  const size_t per_t = static_cast<size_t>(C) *
+                       (static_cast<size_t>(p->rows_alloc) * N + static_cast<size_t>(N) * p->rs + 1);
+  long long nt = static_cast<long long>(p->workspace_budget / (per_t * sizeof(float2)));
+  if (nt < 1) nt = 1;
+  if (nt > n_time) nt = n_time;
+  if (nt > (1 << 20)) nt = 1 << 20;
+  if (p->ws_time < nt) {
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream sync before scratch growth");
+    e = p->d_ws.alloc(per_t * static_cast<size_t>(nt));
+    if (e != cudaSuccess) {
+      p->ws_time = 0;
+      return fail(EPIC_ERR_OOM, "unfused scratch allocation failed");
+    }
+    p->ws_time = static_cast<int>(nt);
+  }
+  nt = std::min<long long>(nt, p->ws_time);
+  epic::UnfusedArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_chan = C;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.grid_n = N;
+  a.cell0 = p->d_cell0.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win = p->d_win.p;
+  a.twid = p->d_twid.p;
+  const size_t cap = static_cast<size_t>(p->ws_time) * C;
+  a.grid = p->d_ws.p;
+  a.spec = a.grid + cap * p->rows_alloc * N;
+  a.pix = a.spec + cap * N * p->rs;
+  a.rows_alloc = p->rows_alloc;
+  a.rs = p->rs;
+  a.image = d_image;
+  a.img_scale = 1.0 / static_cast<double>(n_time);
+  a.do_cal = p->cal ? 1 : 0;
+  a.k0x = p->cal ? p->k0x : 0;
+  a.k0y = p->cal ? p->k0y : 0;
+  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
+  a.kacc = p->d_kacc.p;
+  a.pacc = p->d_pacc.p;
+  for (long long t0 = 0; t0 < n_time; t0 += nt) {
+    const int n = static_cast<int>(std::min<long long>(nt, n_time - t0));
+    EPIC_CUDA(epic::launch_unfused_batch(a, t0, n, p->sms, p->stream));
+  }
+  if (p->cal) p->frames += n_time;
+  return EPIC_OK;
 }
 
 }  // namespace
@@ -164,12 +225,18 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   for (int i = 0; i < 2 * d->n_ant; ++i)
     if (!std::isfinite(d->ant_xy_m[i])) return fail(EPIC_ERR_INVALID_ARG, "non-finite antenna position");
 
+  if (d->path != EPIC_PATH_AUTO && d->path != EPIC_PATH_FUSED && d->path != EPIC_PATH_UNFUSED)
+    return fail(EPIC_ERR_INVALID_ARG, "unknown path");
   epic::ImageKernelShape shape{};
-  if (!epic::image_kernel_shape(d->grid_n, &shape))
-    return fail(EPIC_ERR_UNSUPPORTED, "grid_n must be 16, 32, 64 or 128 in this build");
-  if (d->n_ant > shape.max_ant)
-    return fail(EPIC_ERR_UNSUPPORTED, "n_ant exceeds " + std::to_string(shape.max_ant) +
-                                          " for this grid size");
+  const bool fused_shape = epic::image_kernel_shape(d->grid_n, &shape) && d->n_ant <= shape.max_ant;
+  const bool unfused_ok = epic::unfused_supported(d->grid_n);
+  if (d->path == EPIC_PATH_FUSED && !fused_shape)
+    return fail(EPIC_ERR_UNSUPPORTED, "fused path: grid_n must be 16..128 and n_ant <= " +
+                                          std::to_string(shape.max_ant > 0 ? shape.max_ant : 2048));
+  if (d->path == EPIC_PATH_UNFUSED && !unfused_ok)
+    return fail(EPIC_ERR_UNSUPPORTED, "unfused path: grid_n must be 32..512");
+  if (!fused_shape && !unfused_ok)
+    return fail(EPIC_ERR_UNSUPPORTED, "grid_n must be 16..512 in this build");
 
   epic_plan_s* p = new (std::nothrow) epic_plan_s();
   if (!p) return fail(EPIC_ERR_OOM, "host allocation failed");
@@ -190,6 +257,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     for (int a = 0; a < d->n_ant; ++a) p->flags[a] = d->flags[a] ? 1 : 0;
   p->stream = static_cast<cudaStream_t>(d->cuda_stream);
   p->shape = shape;
+  if (d->workspace_bytes) p->workspace_budget = d->workspace_bytes;
 
   // ---- gridding tables (Eq. 9), FP64 ----
   const int Na = p->na, C = p->nc, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
@@ -276,7 +344,6 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
 
   // ---- launch shape ----
   p->rs = epic::image_rs(p->rows_alloc);
-  p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -287,20 +354,35 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-  if (p->smem > static_cast<size_t>(smem_optin)) {
-    const std::string msg = "array footprint needs " + std::to_string(p->smem) +
-                            " B of shared memory (limit " + std::to_string(smem_optin) + ")";
-    delete p;
-    return fail(EPIC_ERR_UNSUPPORTED, msg);
+  bool fused = fused_shape && d->path != EPIC_PATH_UNFUSED;
+  if (fused) {
+    p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs);
+    if (p->smem > static_cast<size_t>(smem_optin)) {
+      const std::string msg = "array footprint needs " + std::to_string(p->smem) +
+                              " B of shared memory in the fused kernel (limit " +
+                              std::to_string(smem_optin) + ")";
+      if (d->path == EPIC_PATH_FUSED || !unfused_ok) {
+        delete p;
+        return fail(EPIC_ERR_UNSUPPORTED, msg);
+      }
+      fused = false;
+    }
   }
-  int per_sm = 0;
-  e = epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
-  if (e != cudaSuccess || per_sm < 1) {
-    delete p;
-    return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
-                            : fail(EPIC_ERR_UNSUPPORTED, "image kernel cannot be resident");
+  if (fused) {
+    int per_sm = 0;
+    e = epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
+    if (e != cudaSuccess || per_sm < 1) {
+      delete p;
+      return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
+                              : fail(EPIC_ERR_UNSUPPORTED, "image kernel cannot be resident");
+    }
+    p->ctas = per_sm * p->sms;
+    p->path = EPIC_PATH_FUSED;
+  } else {
+    p->smem = 0;
+    p->ctas = p->sms;
+    p->path = EPIC_PATH_UNFUSED;
   }
-  p->ctas = per_sm * p->sms;
 
   // ---- device tables ----
   std::vector<float2> twid(N);
@@ -354,6 +436,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_held.release();
   p->d_stage_in.release();
   p->d_stage_img.release();
+  p->d_ws.release();
   delete p;
   return EPIC_OK;
 }
@@ -379,6 +462,8 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info) {
   info->smem_bytes = p->smem;
   info->frames_pending = p->frames;
   info->iteration = p->iteration;
+  info->path = p->path;
+  info->batch_time = p->ws_time;
   return EPIC_OK;
 }
 
@@ -409,6 +494,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
   const size_t img_bytes = static_cast<size_t>(p->nc) * p->n * p->n * sizeof(double);
   if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_image, 0, img_bytes, p->stream));
+  if (p->path == EPIC_PATH_UNFUSED) return image_unfused(p, d_volt, n_time, d_image);
   epic::ImageArgs a{};
   a.volt = d_volt;
   a.input_fmt = p->input;
@@ -703,6 +789,8 @@ namespace epic {
 int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, double* d_image,
                        double img_scale) {
   if (!p || !d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad batch");
+  if (p->path != EPIC_PATH_FUSED)
+    return fail(EPIC_ERR_UNSUPPORTED, "this call needs a plan on the fused path");
   ImageArgs a{};
   a.volt = d_volt;
   a.input_fmt = p->input;

@@ -1,0 +1,240 @@
+// Plain (unfused) FP32 EPIC imaging path for any grid side N = 32..512.
+//
+// Each step is its own kernel and hands its result to the next through HBM,
+// one batch of frames at a time (frame f = t_local * C + c):
+//   grid_scatter   gain correction (Eq. 8) + gridding (Eq. 9): every
+//                  (frame, antenna, stencil row) adds its K taps to the
+//                  grid window G[f][row][N] with global float atomics;
+//   rows_fft       N-point FFT of every occupied grid row, written
+//                  transposed into Hs[f][kx][row];
+//   cols_fft       N-point FFT of every column (Eq. 10), |E|^2 summed over
+//                  the batch's frames in registers and added to the image;
+//                  the owner of the calibrator pixel stores it per frame;
+//   correlate      EPICal K_a += E_a conj(P), P_a += |E_a|^2 (Eqs. 12, 15).
+// The grid window holds the occupied rows of each channel (as in the fused
+// kernel); the centring signs and 1/Na are folded into the weights.
+#include "epic_fft.cuh"
+#include "epic_internal.h"
+
+namespace epic {
+namespace {
+
+using fft::cmul;
+using fft::kFull;
+
+template <int N> struct UCfg;
+template <> struct UCfg<32>  { static constexpr int N1 = 4,  N2 = 8; };
+template <> struct UCfg<64>  { static constexpr int N1 = 8,  N2 = 8; };
+template <> struct UCfg<128> { static constexpr int N1 = 8,  N2 = 16; };
+template <> struct UCfg<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct UCfg<512> { static constexpr int N1 = 16, N2 = 32; };
+
+constexpr int kUBT = 256;   // threads per CTA of the FFT kernels
+
+__device__ __forceinline__ float2 load_volt_u(const void* volt, int fmt, size_t idx) {
+  if (fmt == 0) {
+    const unsigned b = __ldg(static_cast<const unsigned char*>(volt) + idx);
+    const int re = static_cast<int>(b << 24) >> 28;
+    const int im = static_cast<int>(b << 28) >> 28;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+  return __ldg(static_cast<const float2*>(volt) + idx);
+}
+
+// ---- gridding: one thread per (frame, stencil row, antenna) ----
+__global__ void grid_scatter_kernel(const UnfusedArgs A, long long t0, int nt) {
+  const int Na = A.n_ant, C = A.n_chan, K = A.support, N = A.grid_n;
+  const long long items = static_cast<long long>(nt) * C * K * Na;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long it = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; it < items;
+       it += stride) {
+    const int a = static_cast<int>(it % Na);
+    long long r = it / Na;
+    const int dy = static_cast<int>(r % K);
+    r /= K;
+    const int c = static_cast<int>(r % C);
+    const int tl = static_cast<int>(r / C);
+    const int c0 = __ldg(A.cell0 + static_cast<size_t>(c) * Na + a);
+    if (c0 < 0) continue;
+    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+    const size_t vidx = (static_cast<size_t>(t0 + tl) * C + c) * Na + a;
+    const float2 e = load_volt_u(A.volt, A.input_fmt, vidx);
+    const float2 ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.wgain + static_cast<size_t>(c) * Na + a));
+    const float* w = A.wts + (static_cast<size_t>(c) * Na + a) * K * K + dy * K;
+    const size_t f = static_cast<size_t>(tl) * C + c;
+    float* g = reinterpret_cast<float*>(A.grid + f * A.rows_alloc * N + c0 + dy * N);
+    for (int dx = 0; dx < K; ++dx) {
+      const float wv = __ldg(w + dx);
+      atomicAdd(g + 2 * dx, wv * ec.x);
+      atomicAdd(g + 2 * dx + 1, wv * ec.y);
+    }
+  }
+}
+
+// ---- row FFTs: one N1-lane group per (frame, occupied row) ----
+template <int N>
+__global__ void __launch_bounds__(kUBT) rows_fft_kernel(const UnfusedArgs A, int nt) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
+  constexpr int GROUPS = kUBT / N1;
+  using X = fft::Xchg<N1, N2>;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[GROUPS * X::ZG];
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
+  const unsigned gmask = fft::group_mask<N1>(lane);
+  float2* z = zbuf + g * X::ZG;
+  const int C = A.n_chan;
+  const long long pairs = static_cast<long long>(nt) * C * A.rows_alloc;
+  for (long long pr = static_cast<long long>(blockIdx.x) * GROUPS + g; pr < pairs;
+       pr += static_cast<long long>(gridDim.x) * GROUPS) {
+    const int row = static_cast<int>(pr % A.rows_alloc);
+    const long long f = pr / A.rows_alloc;
+    const int c = static_cast<int>(f % C);
+    if (row >= __ldg(A.win + c).y) continue;        // group-uniform
+    const float2* src = A.grid + (static_cast<size_t>(f) * A.rows_alloc + row) * N;
+    float2 v[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) v[j] = src[n1 + N1 * j];
+    fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
+    float2* dst = A.spec + static_cast<size_t>(f) * N * A.rs + row;
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) dst[static_cast<size_t>(n1 + N1 * h + N2 * k1) * A.rs] = v[h * N1 + k1];
+  }
+}
+
+// ---- column FFTs + |E|^2: unit = (channel, block of GROUPS columns, time segment) ----
+template <int N>
+__global__ void __launch_bounds__(kUBT) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
+  constexpr int GROUPS = kUBT / N1;
+  constexpr int CBLK = (N + GROUPS - 1) / GROUPS;   // column blocks per channel
+  using X = fft::Xchg<N1, N2>;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[GROUPS * X::ZG];
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
+  const unsigned gmask = fft::group_mask<N1>(lane);
+  float2* z = zbuf + g * X::ZG;
+  const int C = A.n_chan;
+  const int units = C * CBLK * segs;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int s = u % segs;
+    const int cb = (u / segs) % CBLK;
+    const int c = u / (segs * CBLK);
+    const int kx = cb * GROUPS + g;
+    const int tb = nt * s / segs, te = nt * (s + 1) / segs;
+    const int2 wn = __ldg(A.win + c);
+    const int y0 = wn.x, R = wn.y;
+    const bool col_ok = kx < N;
+    float acc[N2];
+#pragma unroll
+    for (int q = 0; q < N2; ++q) acc[q] = 0.f;
+    const bool pix_group = A.do_cal && kx == A.k0x;
+    const int pq = A.k0y / N1;
+    const int pslot = (pq % H) * N1 + pq / H;
+    for (int tl = tb; tl < te; ++tl) {
+      if (!col_ok) continue;
+      const size_t f = static_cast<size_t>(tl) * C + c;
+      const float2* src = A.spec + (f * N + kx) * A.rs;
+      float2 v[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) {
+        const int jw = n1 + N1 * j - y0;
+        v[j] = (jw >= 0 && jw < R) ? src[jw] : make_float2(0.f, 0.f);
+      }
+      fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
+#pragma unroll
+      for (int q = 0; q < N2; ++q) acc[q] += v[q].x * v[q].x + v[q].y * v[q].y;
+      if (pix_group && n1 == A.k0y % N1) {
+#pragma unroll
+        for (int q = 0; q < N2; ++q)
+          if (q == pslot) A.pix[f] = make_float2(v[q].x * A.pix_sign, v[q].y * A.pix_sign);
+      }
+    }
+    if (!col_ok) continue;
+    double* img = A.image + static_cast<size_t>(c) * N * N;
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int ky = n1 + N1 * h + N2 * k1;
+        const double v = static_cast<double>(acc[h * N1 + k1]) * A.img_scale;
+        if (segs == 1) img[ky * N + kx] += v;
+        else atomicAdd(img + ky * N + kx, v);
+      }
+  }
+}
+
+// ---- EPICal correlation: one thread per (channel, antenna) over the batch ----
+__global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
+  const int Na = A.n_ant, C = A.n_chan;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C * Na) return;
+  const int c = i / Na, a = i % Na;
+  if (__ldg(A.cell0 + i) < 0) return;
+  const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+  float kr = 0.f, ki = 0.f, pp = 0.f;
+  for (int tl = 0; tl < nt; ++tl) {
+    const size_t f = static_cast<size_t>(tl) * C + c;
+    const float2 p = A.pix[f];
+    const float2 e0 = load_volt_u(A.volt, A.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
+    const float2 e = make_float2(e0.x * vs, e0.y * vs);
+    kr += e.x * p.x + e.y * p.y;
+    ki += e.y * p.x - e.x * p.y;
+    pp += e.x * e.x + e.y * e.y;
+  }
+  A.kacc[i].x += kr;
+  A.kacc[i].y += ki;
+  A.pacc[i] += pp;
+}
+
+template <int N>
+cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
+  const size_t gbytes = static_cast<size_t>(nt) * a.n_chan * a.rows_alloc * N * sizeof(float2);
+  cudaError_t e = cudaMemsetAsync(a.grid, 0, gbytes, s);
+  if (e != cudaSuccess) return e;
+  const long long items = static_cast<long long>(nt) * a.n_chan * a.support * a.n_ant;
+  long long gb = (items + 255) / 256;
+  if (gb > static_cast<long long>(sms) * 16) gb = static_cast<long long>(sms) * 16;
+  grid_scatter_kernel<<<static_cast<unsigned>(gb), 256, 0, s>>>(a, t0, nt);
+  constexpr int GROUPS = kUBT / UCfg<N>::N1;
+  const long long pairs = static_cast<long long>(nt) * a.n_chan * a.rows_alloc;
+  long long rb = (pairs + GROUPS - 1) / GROUPS;
+  if (rb > static_cast<long long>(sms) * 8) rb = static_cast<long long>(sms) * 8;
+  rows_fft_kernel<N><<<static_cast<unsigned>(rb), kUBT, 0, s>>>(a, nt);
+  constexpr int CBLK = (N + GROUPS - 1) / GROUPS;
+  const int base_units = a.n_chan * CBLK;
+  int segs = 1;
+  while (base_units * segs < 4 * sms && segs * 8 <= nt) segs *= 2;
+  const int units = base_units * segs;
+  const int cb = units < sms * 4 ? units : sms * 4;
+  cols_fft_kernel<N><<<cb, kUBT, 0, s>>>(a, nt, segs);
+  if (a.do_cal) {
+    const int n = a.n_chan * a.n_ant;
+    correlate_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, t0, nt);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool unfused_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
+cudaError_t launch_unfused_batch(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
+  switch (a.grid_n) {
+    case 32: return launch_unfused_n<32>(a, t0, nt, sms, s);
+    case 64: return launch_unfused_n<64>(a, t0, nt, sms, s);
+    case 128: return launch_unfused_n<128>(a, t0, nt, sms, s);
+    case 256: return launch_unfused_n<256>(a, t0, nt, sms, s);
+    case 512: return launch_unfused_n<512>(a, t0, nt, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace epic
