@@ -15,8 +15,9 @@ unpack (exhaustive), grid table (properties and special positions), the
 image (visibility route, numpy.fft route, direct O(N^4) sum, phase-ramp
 closed form, source position), the EPICal correlation and update (visibility
 route, zenith single-source limit, noise-free fixed point, damping closed
-form, effective integration time) and the visibility solve (noise-free
-truth).  Nothing in this module is parity-unpinned.
+form, effective integration time), the visibility solve (noise-free
+truth) and the chi^2 model image and gradient (noise-free identity, central
+finite differences).  Nothing in this module is parity-unpinned.
 """
 from __future__ import annotations
 
@@ -30,7 +31,8 @@ __all__ = [
     "dirty_image", "calibrator_pixel", "pixel_row", "model_visibilities",
     "cal_denominator", "correlate", "epical_update", "image_interval",
     "epical_interval", "visibilities", "visibility_solve", "gain_error",
-    "align_phase", "Plan", "image_pixels", "correlate_sampled",
+    "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
+    "model_image", "chi2_loss", "chi2_gradient",
 ]
 
 
@@ -452,3 +454,74 @@ def gain_error(g_est: np.ndarray, g_true: np.ndarray) -> float:
     g_est = np.atleast_2d(g_est)
     g_true = np.atleast_2d(g_true)
     return float(np.sqrt(np.mean(np.abs(g_est - g_true) ** 2 / np.abs(g_true) ** 2)))
+
+
+# --------------------------------------------------------------------------
+# differentiation form: chi^2 between the dirty image and a sky-model image
+# --------------------------------------------------------------------------
+def pixel_matrix(plan: Plan, c: int) -> np.ndarray:
+    """A_{k,a} for every pixel k of channel c ([N*N][Na], k = ky*N + kx):
+    the response of pixel k to antenna a through gridding (Eq. 9) and the
+    Eq. 10 transform, E'(s_k) = sum_a A_{k,a} E'_a.  Explicit sums over taps."""
+    N = plan.N
+    K = plan.W.shape[-1]
+    h = (K - 1) // 2
+    A = np.zeros((N * N, plan.Na), np.complex128)
+    ky, kx = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    ky = ky.ravel() - N // 2
+    kx = kx.ravel() - N // 2
+    for a in range(plan.Na):
+        if plan.flags[a]:
+            continue
+        for dy in range(K):
+            for dx in range(K):
+                jx = plan.base[c, a, 0] + dx - h - N // 2
+                jy = plan.base[c, a, 1] + dy - h - N // 2
+                m = np.mod(jx * kx + jy * ky, N)
+                A[:, a] += plan.W[c, a, dy, dx] * np.exp(2j * np.pi * m / N)
+    return A / plan.norm
+
+
+def model_image(plan: Plan, sky_lmS: np.ndarray) -> np.ndarray:
+    """Sky-model dirty image [C][N][N]: the Eq. 8-10 imaging operator applied
+    to the model visibilities, M_k = sum_ab A_{k,a} conj(A_{k,b}) V^M_ab with
+    V^M_ab = sum_s S_s e_a conj(e_b), e_a = exp(-2 pi i u_a . s), i.e.
+    M_k = sum_s S_s |sum_a A_{k,a} e_a|^2 (perfectly calibrated, noise free)."""
+    C = len(plan.freqs)
+    out = np.zeros((C, plan.N, plan.N))
+    for c in range(C):
+        A = pixel_matrix(plan, c)
+        uv = antenna_uv(plan.ant, plan.freqs[c])
+        for l, m, S in np.asarray(sky_lmS, np.float64):
+            e = np.exp(-2j * np.pi * (uv[:, 0] * l + uv[:, 1] * m))
+            out[c] += S * (np.abs(A @ e) ** 2).reshape(plan.N, plan.N)
+    return out
+
+
+def chi2_loss(plan: Plan, E: np.ndarray, g: np.ndarray, M: np.ndarray) -> float:
+    """L = sum_c sum_k (I_k(g) - M_k)^2 with I the dirty image of Eqs. 8-10
+    and the square-and-average step.  E: [T][C][Na], g: [C][Na]."""
+    img, _ = image_interval(plan, E, g)
+    return float(np.sum((img - M) ** 2))
+
+
+def chi2_gradient(plan: Plan, E: np.ndarray, g: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """Gradient of chi2_loss with respect to the complex gains, returned in
+    the convention grad = 2 dL/dconj(g) (so that dL = Re(conj(grad) dg)).
+    With w = 1/g, E'(s_k, t) = sum_a A_{k,a} w_a E_a(t) and R_k = dL/dI_k =
+    2 (I_k - M_k):  dL/dconj(w_a) = (1/T) sum_t conj(E_a(t)) sum_k
+    conj(A_{k,a}) R_k E'(s_k, t),  dL/dconj(g_a) = dL/dconj(w_a) (-1/conj(g_a)^2).
+    Evaluated with explicit A_{k,a} (tiny arrays only)."""
+    T, C, Na = E.shape
+    img, _ = image_interval(plan, E, g)
+    out = np.zeros((C, Na), np.complex128)
+    for c in range(C):
+        A = pixel_matrix(plan, c)
+        R = 2.0 * (img[c] - M[c]).ravel()
+        w = 1.0 / g[c]
+        Eimg = (E[:, c, :] * w) @ A.T                 # [T][N*N]
+        Y = (R[None, :] * Eimg) @ np.conj(A)          # [T][Na]
+        dw = np.sum(np.conj(E[:, c, :]) * Y, axis=0) / T
+        out[c] = 2.0 * dw * (-1.0 / np.conj(g[c]) ** 2)
+    out[:, plan.flags] = 0.0
+    return out

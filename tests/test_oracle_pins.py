@@ -361,3 +361,55 @@ def test_gain_error_metric():
     ge = np.array([[1.1 + 1.1j, 2.0 + 0.2j]])
     # |0.1(1+i)|^2/|1+i|^2 = 0.01 ; |0.2i|^2/4 = 0.01
     assert np.isclose(O.gain_error(ge, gt), 0.1)
+
+
+# --------------------------------------------------------------------------
+# differentiation form (chi^2 gradient)
+# --------------------------------------------------------------------------
+def _diff_case(seed=12, Na=9, N=16, T=40):
+    rng = np.random.default_rng(seed)
+    ant = synth.layout_disc(Na, 8.0, rng, 1.0)
+    f = [48e6, 66e6]
+    g_true = synth.true_gains(2, Na, rng)
+    sky = np.array([[0.0, 0.0, 3.0], [0.2, -0.15, 1.5], [-0.3, 0.25, 0.7]])
+    E = synth.voltages(ant, f, g_true, sky, T, 0.3, rng)
+    flags = np.zeros(Na, bool)
+    flags[4] = True
+    plan = O.Plan(ant, f, N, 0.5, flags=flags)
+    M = O.model_image(plan, sky)
+    return plan, E, g_true, M, rng
+
+
+def test_model_image_equals_noise_free_unit_modulus_image():
+    """The model image is the dirty image of perfectly calibrated, noise-free
+    unit-modulus data of one source (Sec. 2.1 image of visibilities)."""
+    rng = np.random.default_rng(13)
+    ant = synth.layout_disc(10, 8.0, rng, 1.0)
+    sky = np.array([[0.25, -0.1, 2.0]])
+    g = synth.true_gains(1, 10, rng)
+    E = synth.voltages(ant, [55e6], g, sky, 16, 0.0, rng, unit_modulus=True)
+    plan = O.Plan(ant, [55e6], 16, 0.5)
+    img, _ = O.image_interval(plan, E, g)
+    M = O.model_image(plan, sky)
+    assert np.max(np.abs(img - M)) <= 1e-12 * np.max(M)
+    # so the chi^2 gradient vanishes at the true gains
+    assert np.max(np.abs(O.chi2_gradient(plan, E, g, M))) < 1e-10
+
+
+def test_chi2_gradient_matches_finite_differences():
+    """dL = Re(conj(grad) dg) for real and imaginary steps of 1e-6 (central
+    differences of the oracle's own loss)."""
+    plan, E, g_true, M, rng = _diff_case()
+    g = g_true * (1 + 0.1 * (rng.normal(size=g_true.shape) + 1j * rng.normal(size=g_true.shape)))
+    grad = O.chi2_gradient(plan, E, g, M)
+    h = 1e-6
+    for c, a in [(0, 0), (1, 3), (1, 8), (0, 4)]:
+        for d in (h, 1j * h):
+            gp = g.copy()
+            gm = g.copy()
+            gp[c, a] += d
+            gm[c, a] -= d
+            fd = (O.chi2_loss(plan, E, gp, M) - O.chi2_loss(plan, E, gm, M)) / 2
+            pred = np.real(np.conj(grad[c, a]) * d)
+            assert abs(fd - pred) <= 1e-6 * abs(grad[c, a]) * h + 1e-12, (c, a, d, fd, pred)
+    assert np.all(grad[:, 4] == 0)
