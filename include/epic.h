@@ -192,6 +192,24 @@ epic_status epical_get_state(epic_plan_t plan, void* buf, size_t* bytes);
  * Errors: INVALID_ARG (size or header mismatch).  Synchronous. */
 epic_status epical_set_state(epic_plan_t plan, const void* buf, size_t bytes);
 
+/* Set the gains from device memory (d_gains: device [C][Na] complex128),
+ * asynchronously on the plan stream; w = 1/g is formed on the device.  Zero
+ * gains give non-finite multipliers (no check, no host round trip). */
+epic_status epic_set_gains_device(epic_plan_t plan, const double* d_gains);
+
+/* Differentiation form: gradient of a real loss L(I) of the dirty image
+ * with respect to the complex gains.  Given d_dl_di = dL/dI (device
+ * [C][N][N] float64, I as produced by epic_image on the same d_volt and the
+ * plan's current gains), writes d_grad_g (device [C][Na] complex128) =
+ * 2 dL/dconj(g), the convention of torch complex autograd, so that
+ * dL = Re(conj(grad) dg).  Through w = 1/g (Eq. 8) and Eqs. 9-10:
+ * dL/dconj(w_a) = (1/T) sum_t conj(E_a(t)) sum_k conj(A_{k,a}) R_k E'(s_k,t),
+ * R = dL/dI, evaluated as inverse FFTs of R . E' followed by degridding;
+ * every frame is recomputed, none is stored.  Flagged antennas get 0.
+ * Fused path only (N <= 128), else UNSUPPORTED.  Asynchronous. */
+epic_status epic_image_backward(epic_plan_t plan, const void* d_volt, long long n_time,
+                                const double* d_dl_di, double* d_grad_g);
+
 /* Debug/test accessors (synchronous, host outputs). */
 /* base_xy: host [C][Na][2] int32 stencil-centre cell (x, y); w: host
  * [C][Na][K][K] float64 normalised tap weights ([dy][dx]); either may be

@@ -27,6 +27,7 @@ EXPORTS = [
     "epical_configure", "epical_update",
     "epic_plan_sync", "epical_get_gains", "epical_get_state", "epical_set_state",
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
+    "epic_set_gains_device", "epic_image_backward",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -98,6 +99,8 @@ def load(path: str | None = None) -> ct.CDLL:
         "epical_set_state": [P, P, ct.c_size_t],
         "epic_plan_get_grid_table": [P, c_ip, c_dp],
         "epic_unpack_ci4": [P, P, P, ct.c_longlong],
+        "epic_set_gains_device": [P, P],
+        "epic_image_backward": [P, P, ct.c_longlong, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -178,6 +178,23 @@ class Plan:
                                                  int(bool(accumulate))))
         return image
 
+    def set_gains_device(self, gains):
+        """Set g from a device complex128 [C][Na] tensor (asynchronous)."""
+        torch = _torch()
+        B.check(self._lib.epic_set_gains_device(self.handle, _dptr(gains, torch.complex128, "gains")))
+
+    def image_backward(self, volt, dl_di, grad=None):
+        """2 dL/dconj(g) for dl_di = dL/dI (float64 [C][N][N], device)."""
+        torch = _torch()
+        if grad is None:
+            grad = torch.empty((self.n_chan, self.n_ant), dtype=torch.complex128, device=volt.device)
+        want = torch.uint8 if self.input == "ci4" else torch.complex64
+        B.check(self._lib.epic_image_backward(self.handle, _dptr(volt, want, "volt"),
+                                              int(volt.shape[0]),
+                                              _dptr(dl_di, torch.float64, "dl_di"),
+                                              _dptr(grad, torch.complex128, "grad")))
+        return grad
+
     def configure(self, cal_lm, model_lmS, gamma, g0=None):
         src = _f64(model_lmS).reshape(-1, 3)
         g = None if g0 is None else _c128_as_f64(g0, self.n_chan * self.n_ant)

@@ -69,6 +69,29 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 
 cudaError_t launch_unpack(const unsigned char* in, float2* out, long long n, cudaStream_t s);
 
+// Adjoint (gain gradient) launch of the fused structure, N <= 128.
+struct AdjointArgs {
+  const void* volt;
+  int input_fmt;
+  long long n_time;
+  int n_chan, n_ant, support;
+  const int* cell0;
+  const float* wts;
+  const float2* wgain;
+  const float* vscale;
+  const int2* win;
+  const float2* twid;
+  const double* dldi;      // [C][N][N] dL/dI
+  double2* dldw;           // [C][Na] accumulated dL/dconj(w), pre-zeroed
+  double img_scale;        // 1 / T
+  int segs, rows_alloc, rs, grid;
+  size_t smem;
+};
+cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
+                                    const unsigned char* flags, double2* out, cudaStream_t s);
+cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s);
+
 // Arguments of one batch of the plain unfused path (epic_unfused.cu).
 struct UnfusedArgs {
   const void* volt;        // device [T][C][Na] (whole call; batches index into it)

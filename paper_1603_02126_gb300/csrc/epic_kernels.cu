@@ -67,6 +67,18 @@ __device__ __forceinline__ void fft_group(float2 (&v)[Geo<N>::N2], int n1, float
   fft::fft_lanes<Geo<N>::N1, Geo<N>::N2>(v, n1, z, tw, gmask);
 }
 
+__device__ __forceinline__ float2 load_volt(const void* volt, int fmt, int n_chan, int n_ant,
+                                           long long t, int c, int a) {
+  const size_t idx = (static_cast<size_t>(t) * n_chan + c) * n_ant + a;
+  if (fmt == 0) {
+    const unsigned b = __ldg(static_cast<const unsigned char*>(volt) + idx);
+    const int re = static_cast<int>(b << 24) >> 28;
+    const int im = static_cast<int>(b << 28) >> 28;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+  return __ldg(static_cast<const float2*>(volt) + idx);
+}
+
 __device__ __forceinline__ float2 load_volt(const ImageArgs& A, long long t, int c, int a) {
   const size_t idx = (static_cast<size_t>(t) * A.n_chan + c) * A.n_ant + a;
   if (A.input_fmt == 0) {
@@ -292,6 +304,249 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
   }
 }
 
+// Adjoint of the imaging chain (differentiation form).  With R = dL/dI for
+// the dirty image I, X(t) the raw FFT of the folded grid of frame t, and
+// W'_a the folded stencil weights, the gradient of L with respect to the
+// conjugate gain multipliers is
+//   dL/dconj(w_a) = (1/T) sum_t conj(E_a(t)) sum_j W'_a(j) [F^- (R . X(t))]_j
+// (F^- = the conjugate transform).  Every frame is recomputed (nothing is
+// stored): scatter, row FFTs, column FFTs, multiply by R, inverse column
+// FFTs into the grid window, inverse row FFTs, gather of the K x K taps per
+// antenna.  R for the unit's channel stays in registers.
+template <int N, int MAXA>
+__global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const AdjointArgs A) {
+  using G = Geo<N>;
+  constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][N]
+  float2* Tt = Wg + A.rows_alloc * N;                  // [N][rs] or [rows][N]
+  float2* Z = Tt + N * A.rs;
+  float2* tw = Z + GROUPS * G::ZG;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int g = tid / N1;
+  const int n1 = tid % N1;
+  const unsigned gmask = fft::group_mask<N1>(lane);
+  float2* zg = Z + g * G::ZG;
+
+  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
+  for (int i = tid; i < A.rows_alloc * N; i += BT) Wg[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const int Na = A.n_ant;
+  const int K = A.support;
+  const int KK = K * K;
+  const int items = K * Na;
+  const int items_pad = ((items + BT - 1) / BT) * BT;
+  const long long T = A.n_time;
+  const int units = A.n_chan * A.segs;
+
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int c = u / A.segs;
+    const int s = u - c * A.segs;
+    const long long t0 = T * s / A.segs;
+    const long long t1 = T * (s + 1) / A.segs;
+    if (t0 >= t1) continue;
+    const int2 wn = __ldg(A.win + c);
+    const int y0 = wn.x, R = wn.y;
+    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+    const int* cell0 = A.cell0 + static_cast<size_t>(c) * Na;
+    const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
+    const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
+    const double* rimg = A.dldi + static_cast<size_t>(c) * N * N;
+
+    // R_k for this thread's pixels, in the column-FFT output order
+    float rk[G::NACC];
+#pragma unroll
+    for (int r = 0; r < G::COLROUNDS; ++r) {
+      const int kx = g + GROUPS * r;
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const int ky = n1 + N1 * h + N2 * k1;
+          rk[r * N2 + h * N1 + k1] = static_cast<float>(__ldg(rimg + ky * N + kx));
+        }
+    }
+    float2 gac[MAXA], ecur[MAXA];
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      gac[i] = make_float2(0.f, 0.f);
+      ecur[i] = make_float2(0.f, 0.f);
+    }
+
+    for (long long t = t0; t < t1; ++t) {
+      // ---- A: raw voltages, gain + scatter (as the forward pass) ----
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const int a = tid + BT * i;
+        if (a < Na) {
+          const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t, c, a);
+          ecur[i] = make_float2(e.x * vs, e.y * vs);
+        }
+      }
+      for (int it = tid; it < items_pad; it += BT) {
+        const bool in = it < items;
+        const int a = in ? it % Na : 0;
+        const int dy = in ? it / Na : 0;
+        const int c0 = in ? __ldg(cell0 + a) : -1;
+        if (c0 >= 0) {
+          const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t, c, a);
+          const float2 ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
+          const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
+          const int rowcell = c0 + dy * N;
+          for (int dx = 0; dx < K; ++dx) {
+            const float w = __ldg(wrow + dx);
+            atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
+            atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
+          }
+        }
+      }
+      __syncthreads();
+
+      // ---- B: row FFTs into the transposed buffer ----
+      for (int row = g; row < R; row += GROUPS) {
+        float2 v[N2];
+        float2* wr = Wg + row * N;
+#pragma unroll
+        for (int j = 0; j < N2; ++j) v[j] = wr[n1 + N1 * j];
+#pragma unroll
+        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+        fft_group<N>(v, n1, zg, tw, gmask);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) Tt[(n1 + N1 * h + N2 * k1) * A.rs + row] = v[h * N1 + k1];
+      }
+      __syncthreads();
+
+      // ---- C: column FFTs, multiply by R, inverse column FFTs into the window ----
+#pragma unroll
+      for (int r = 0; r < G::COLROUNDS; ++r) {
+        const int kx = g + GROUPS * r;
+        float2 v[N2];
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const int jw = n1 + N1 * j - y0;
+          v[j] = (jw >= 0 && jw < R) ? Tt[kx * A.rs + jw] : make_float2(0.f, 0.f);
+        }
+        fft_group<N>(v, n1, zg, tw, gmask);
+        // output slot h*N1 + k1 holds ky = n1 + N1*(h + H*k1): the inverse
+        // transform's input slot j = h + H*k1; conjugate for F^-
+        float2 u[N2];
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const float rv = rk[r * N2 + h * N1 + k1];
+            const float2 x = v[h * N1 + k1];
+            u[h + H * k1] = make_float2(x.x * rv, -x.y * rv);
+          }
+        fft_group<N>(u, n1, zg, tw, gmask);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const int jw = n1 + N1 * h + N2 * k1 - y0;
+            if (jw >= 0 && jw < R) {
+              const float2 x = u[h * N1 + k1];
+              Wg[jw * N + kx] = make_float2(x.x, -x.y);
+            }
+          }
+      }
+      __syncthreads();
+
+      // ---- D: inverse row FFTs of the window rows, row-major into Tt ----
+      for (int row = g; row < R; row += GROUPS) {
+        float2 v[N2];
+        float2* wr = Wg + row * N;
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const float2 x = wr[n1 + N1 * j];
+          v[j] = make_float2(x.x, -x.y);
+        }
+#pragma unroll
+        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+        fft_group<N>(v, n1, zg, tw, gmask);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const float2 x = v[h * N1 + k1];
+            Tt[row * N + n1 + N1 * h + N2 * k1] = make_float2(x.x, -x.y);
+          }
+      }
+      __syncthreads();
+
+      // ---- E: degrid and accumulate conj(E_a) Y_a ----
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const int a = tid + BT * i;
+        if (a < Na) {
+          const int c0 = __ldg(cell0 + a);
+          if (c0 >= 0) {
+            const float* wa = wts + static_cast<size_t>(a) * KK;
+            float yr = 0.f, yi = 0.f;
+            for (int dy = 0; dy < K; ++dy)
+              for (int dx = 0; dx < K; ++dx) {
+                const float w = __ldg(wa + dy * K + dx);
+                const float2 b = Tt[c0 + dy * N + dx];
+                yr += w * b.x;
+                yi += w * b.y;
+              }
+            const float2 e = ecur[i];
+            gac[i].x += e.x * yr + e.y * yi;     // conj(e) * y
+            gac[i].y += e.x * yi - e.y * yr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
+      if (a < Na && cell0[a] >= 0) {
+        const size_t o = static_cast<size_t>(c) * Na + a;
+        atomicAdd(&A.dldw[o].x, static_cast<double>(gac[i].x) * A.img_scale);
+        atomicAdd(&A.dldw[o].y, static_cast<double>(gac[i].y) * A.img_scale);
+      }
+    }
+  }
+}
+
+// grad = 2 dL/dconj(g) = 2 dL/dconj(w) * (-1 / conj(g)^2); flagged -> 0.
+__global__ void adjoint_finalize_kernel(int n, int n_ant, const double2* __restrict__ dldw,
+                                        const double2* __restrict__ gain,
+                                        const unsigned char* __restrict__ flags,
+                                        double2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (flags[i % n_ant]) {
+    out[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double2 g = gain[i];
+  // conj(g)^2 = (gr^2 - gi^2) - 2 i gr gi ; -1 / conj(g)^2 = -conj(g^2)/|g|^4 ... as (qr, qi)
+  const double ar = g.x * g.x - g.y * g.y, ai = -2.0 * g.x * g.y;   // conj(g)^2
+  const double den = ar * ar + ai * ai;
+  const double qr = -ar / den, qi = ai / den;                       // -1 / conj(g)^2
+  const double2 d = dldw[i];
+  out[i] = make_double2(2.0 * (d.x * qr - d.y * qi), 2.0 * (d.x * qi + d.y * qr));
+}
+
+// g and w = 1/g from device gains (no host round trip).
+__global__ void set_gains_kernel(int n, const double2* __restrict__ g_in, double2* __restrict__ g,
+                                 float2* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = g_in[i];
+  const double m2 = v.x * v.x + v.y * v.y;
+  g[i] = v;
+  w[i] = make_float2(static_cast<float>(v.x / m2), static_cast<float>(-v.y / m2));
+}
+
 // EPICal update (Eqs. 15-17) in FP64, one thread per (channel, antenna).
 __global__ void epical_update_kernel(const UpdateArgs A) {
   const int n = A.n_chan * A.n_ant;
@@ -378,7 +633,46 @@ void shape_n(ImageKernelShape* o) {
   o->max_ant = Cfg<N>::BT * kMaxAntPerThread;
 }
 
+template <int N>
+cudaError_t adjoint_n(const AdjointArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  if (a.n_ant <= Cfg<N>::BT) {
+    e = cudaFuncSetAttribute(epic_image_adjoint<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(a.smem));
+    if (e != cudaSuccess) return e;
+    epic_image_adjoint<N, 1><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(epic_image_adjoint<N, kMaxAntPerThread>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(a.smem));
+    if (e != cudaSuccess) return e;
+    epic_image_adjoint<N, kMaxAntPerThread><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 16: return adjoint_n<16>(a, s);
+    case 32: return adjoint_n<32>(a, s);
+    case 64: return adjoint_n<64>(a, s);
+    case 128: return adjoint_n<128>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
+                                    const unsigned char* flags, double2* out, cudaStream_t s) {
+  const int n = n_chan * n_ant;
+  adjoint_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, n_ant, dldw, gain, flags, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s) {
+  set_gains_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, g_in, g, w);
+  return cudaGetLastError();
+}
 
 bool image_kernel_shape(int n, ImageKernelShape* out) {
   switch (n) {

@@ -115,6 +115,9 @@ struct epic_plan_s {
   size_t workspace_budget = static_cast<size_t>(2) << 30;
   DevBuf<float2> d_ws;          // [nt*C] x (rows_alloc*N + N*rs + 1)
   int ws_time = 0;              // time samples the scratch holds
+
+  // differentiation form
+  DevBuf<double2> d_dldw;       // [C][Na] dL/dconj(w) accumulator
 };
 
 namespace {
@@ -437,6 +440,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_stage_in.release();
   p->d_stage_img.release();
   p->d_ws.release();
+  p->d_dldw.release();
   delete p;
   return EPIC_OK;
 }
@@ -764,6 +768,55 @@ epic_status epical_set_state(epic_plan_t p, const void* buf, size_t bytes) {
   p->gamma = hd.gamma;
   p->frames = hd.frames;
   p->iteration = hd.iteration;
+  return EPIC_OK;
+}
+
+epic_status epic_set_gains_device(epic_plan_t p, const double* d_gains) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_gains) return fail(EPIC_ERR_INVALID_ARG, "d_gains is NULL");
+  EPIC_CUDA(epic::launch_set_gains(p->nc * p->na, reinterpret_cast<const double2*>(d_gains), p->d_gain.p,
+                                   p->d_wgain.p, p->stream));
+  return EPIC_OK;
+}
+
+epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_time,
+                                const double* d_dl_di, double* d_grad_g) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_volt || !d_dl_di || !d_grad_g) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
+  if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
+  if (p->path != EPIC_PATH_FUSED)
+    return fail(EPIC_ERR_UNSUPPORTED, "the adjoint is built for the fused path (N <= 128)");
+  const size_t n = static_cast<size_t>(p->nc) * p->na;
+  if (!p->d_dldw.p) {
+    cudaError_t e = p->d_dldw.alloc(n);
+    if (e != cudaSuccess) return fail(EPIC_ERR_OOM, "gradient scratch allocation failed");
+  }
+  EPIC_CUDA(cudaMemsetAsync(p->d_dldw.p, 0, n * sizeof(double2), p->stream));
+  epic::AdjointArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.cell0 = p->d_cell0.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win = p->d_win.p;
+  a.twid = p->d_twid.p;
+  a.dldi = d_dl_di;
+  a.dldw = p->d_dldw.p;
+  a.img_scale = 1.0 / static_cast<double>(n_time);
+  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.rows_alloc = p->rows_alloc;
+  a.rs = p->rs;
+  const long long units = static_cast<long long>(p->nc) * a.segs;
+  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
+  a.smem = p->smem;
+  EPIC_CUDA(epic::launch_adjoint(p->n, a, p->stream));
+  EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_flags.p,
+                                          reinterpret_cast<double2*>(d_grad_g), p->stream));
   return EPIC_OK;
 }
 
