@@ -92,6 +92,16 @@ typedef struct {
   int batch_time;              /* UNFUSED: time samples per batch (0 before use) */
 } epic_plan_info;
 
+/* Result of epic_autotune. */
+typedef struct {
+  int path;                    /* epic_path that was tuned */
+  int units_target;            /* FUSED: work units per CTA aimed for */
+  int batch_time;              /* UNFUSED: time samples per batch (0 = scratch budget) */
+  int cols_target;             /* UNFUSED: column-FFT units per SM aimed for */
+  double ms_default, ms_best;  /* epic_image time before / after tuning */
+  int candidates;              /* launch shapes timed */
+} epic_tune_result;
+
 /* Build the gridding tables of Eq. 9 for every (channel, antenna): the
  * stencil centre is the nearest cell to u_a/du + N/2 (u_a = r_a f / c),
  * taps are normalised to sum 1 (W(0) = 1, Sec. 2.1).  Uploads tables and
@@ -151,6 +161,30 @@ epic_status epic_image_host(epic_plan_t plan, const void* h_volt, long long n_ti
  * Synchronous. */
 epic_status epic_image_host_static(epic_plan_t plan, const void* h_volt, long long n_time,
                                    double* h_image, int accumulate);
+
+/* Batching form, autotuner: times candidate launch shapes of epic_image on
+ * this batch (FUSED: work units per CTA, i.e. the time-segment length of a
+ * persistent CTA's work unit; UNFUSED: time samples per batch and
+ * column-FFT work units per SM), keeps the fastest in the plan and reports
+ * it in *out (may be NULL).  d_image is overwritten; EPICal sums are left
+ * untouched.  Synchronous.  The paper has no counterpart (run-time tuning
+ * of this implementation). */
+epic_status epic_autotune(epic_plan_t plan, const void* d_volt, long long n_time, double* d_image,
+                          epic_tune_result* out);
+
+/* Batching form, CUDA graph: capture one calibration interval, epic_image
+ * of d_volt (n_time samples, all channels) into d_image followed, when
+ * EPICal is configured, by epical_update writing d_gains_out (may be NULL),
+ * into a graph owned by the plan.  Buffers are bound at capture; the plan
+ * stream must not be the legacy default stream.  Replace the graph by
+ * capturing again.  Synchronous. */
+epic_status epic_graph_capture(epic_plan_t plan, const void* d_volt, long long n_time, double* d_image,
+                               double* d_gains_out);
+
+/* Replay the captured interval on the plan stream (one interval: image and,
+ * if configured, the gain update).  Asynchronous.  Errors: STATE if no
+ * graph was captured. */
+epic_status epic_graph_launch(epic_plan_t plan);
 
 /* Arm EPICal (Sec. 2.2).  (cal_l, cal_m): calibrator direction; the pixel
  * used is the nearest pixel centre.  Model: n_src point sources, host

@@ -27,7 +27,8 @@ EXPORTS = [
     "epical_configure", "epical_update",
     "epic_plan_sync", "epical_get_gains", "epical_get_state", "epical_set_state",
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
-    "epic_set_gains_device", "epic_image_backward",
+    "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
+    "epic_graph_launch",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -59,6 +60,14 @@ class PlanInfo(ct.Structure):
         ("units_per_chan", ct.c_int), ("smem_bytes", ct.c_size_t),
         ("frames_pending", ct.c_longlong), ("iteration", ct.c_longlong),
         ("path", ct.c_int), ("batch_time", ct.c_int),
+    ]
+
+
+class TuneResult(ct.Structure):
+    _fields_ = [
+        ("path", ct.c_int), ("units_target", ct.c_int), ("batch_time", ct.c_int),
+        ("cols_target", ct.c_int), ("ms_default", ct.c_double), ("ms_best", ct.c_double),
+        ("candidates", ct.c_int),
     ]
 
 
@@ -101,6 +110,9 @@ def load(path: str | None = None) -> ct.CDLL:
         "epic_unpack_ci4": [P, P, P, ct.c_longlong],
         "epic_set_gains_device": [P, P],
         "epic_image_backward": [P, P, ct.c_longlong, P, P],
+        "epic_autotune": [P, P, ct.c_longlong, P, ct.POINTER(TuneResult)],
+        "epic_graph_capture": [P, P, ct.c_longlong, P, P],
+        "epic_graph_launch": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

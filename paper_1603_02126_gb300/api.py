@@ -195,6 +195,27 @@ class Plan:
                                               _dptr(grad, torch.complex128, "grad")))
         return grad
 
+    def autotune(self, volt, image=None) -> dict:
+        """Time launch-shape candidates on this batch and keep the fastest."""
+        torch = _torch()
+        if image is None:
+            image = torch.empty((self.n_chan, self.grid_n, self.grid_n), dtype=torch.float64,
+                                device=volt.device)
+        r = B.TuneResult()
+        B.check(self._lib.epic_autotune(self.handle, _dptr(volt, None, "volt"), int(volt.shape[0]),
+                                        _dptr(image, torch.float64, "image"), ct.byref(r)))
+        return {k: getattr(r, k) for k, _ in B.TuneResult._fields_}
+
+    def graph_capture(self, volt, image, gains_out=None):
+        """Capture one interval (image + update) into a CUDA graph."""
+        torch = _torch()
+        B.check(self._lib.epic_graph_capture(self.handle, _dptr(volt, None, "volt"), int(volt.shape[0]),
+                                             _dptr(image, torch.float64, "image"),
+                                             _dptr(gains_out, torch.complex128, "gains_out")))
+
+    def graph_launch(self):
+        B.check(self._lib.epic_graph_launch(self.handle))
+
     def configure(self, cal_lm, model_lmS, gamma, g0=None):
         src = _f64(model_lmS).reshape(-1, 3)
         g = None if g0 is None else _c128_as_f64(g0, self.n_chan * self.n_ant)

@@ -113,6 +113,7 @@ struct UnfusedArgs {
   float pix_sign;
   double2* kacc;
   double* pacc;
+  int cols_target;         // column-FFT work units per SM to aim for
 };
 bool unfused_supported(int n);
 // Enqueue the four kernels of one batch of nt time samples starting at t0.

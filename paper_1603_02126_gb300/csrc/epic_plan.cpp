@@ -118,6 +118,13 @@ struct epic_plan_s {
 
   // differentiation form
   DevBuf<double2> d_dldw;       // [C][Na] dL/dconj(w) accumulator
+
+  // launch-shape parameters (autotuner) and the captured interval graph
+  int tune_units = 4;           // fused: work units per CTA to aim for
+  int tune_nt = 0;              // unfused: time samples per batch (0 = budget)
+  int tune_cols = 4;            // unfused: column units per SM to aim for
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -129,15 +136,15 @@ epic_status check_plan(epic_plan_t p) {
 
 // Segments per channel: enough work units to fill every CTA a few times,
 // preferring a total that is a multiple of the CTA count.
-int choose_segments(int n_chan, long long n_time, int ctas) {
+int choose_segments(int n_chan, long long n_time, int ctas, int target = 4) {
   long long best = 1;
   const long long min_len = 16;
   for (long long s = 1; s <= 4096; ++s) {
     if (n_time / s < min_len && s > 1) break;
     best = s;
     const long long units = static_cast<long long>(n_chan) * s;
-    if (units >= 4LL * ctas && units % ctas == 0) return static_cast<int>(s);
-    if (units >= 16LL * ctas) return static_cast<int>(s);
+    if (units >= static_cast<long long>(target) * ctas && units % ctas == 0) return static_cast<int>(s);
+    if (units >= 4LL * target * ctas) return static_cast<int>(s);
   }
   return static_cast<int>(best);
 }
@@ -148,6 +155,7 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   const size_t per_t = static_cast<size_t>(C) *
                        (static_cast<size_t>(p->rows_alloc) * N + static_cast<size_t>(N) * p->rs + 1);
   long long nt = static_cast<long long>(p->workspace_budget / (per_t * sizeof(float2)));
+  if (p->tune_nt > 0 && p->tune_nt < nt) nt = p->tune_nt;
   if (nt < 1) nt = 1;
   if (nt > n_time) nt = n_time;
   if (nt > (1 << 20)) nt = 1 << 20;
@@ -189,6 +197,7 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
   a.kacc = p->d_kacc.p;
   a.pacc = p->d_pacc.p;
+  a.cols_target = p->tune_cols;
   for (long long t0 = 0; t0 < n_time; t0 += nt) {
     const int n = static_cast<int>(std::min<long long>(nt, n_time - t0));
     EPIC_CUDA(epic::launch_unfused_batch(a, t0, n, p->sms, p->stream));
@@ -441,6 +450,8 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_stage_img.release();
   p->d_ws.release();
   p->d_dldw.release();
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
   delete p;
   return EPIC_OK;
 }
@@ -520,7 +531,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
   a.kacc = p->d_kacc.p;
   a.pacc = p->d_pacc.p;
-  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
   a.rows_alloc = p->rows_alloc;
   a.rs = p->rs;
   const long long units = static_cast<long long>(p->nc) * a.segs;
@@ -771,6 +782,158 @@ epic_status epical_set_state(epic_plan_t p, const void* buf, size_t bytes) {
   return EPIC_OK;
 }
 
+namespace {
+
+// Median device time of `reps` epic_image calls on the plan stream.
+epic_status time_image(epic_plan_t p, const void* d_volt, long long n_time, double* d_image, int reps,
+                       double* ms_out) {
+  cudaEvent_t e0, e1;
+  EPIC_CUDA(cudaEventCreate(&e0));
+  EPIC_CUDA(cudaEventCreate(&e1));
+  std::vector<float> ms;
+  epic_status st = epic_image(p, d_volt, n_time, d_image, 0);   // warm-up (and scratch growth)
+  for (int r = 0; r < reps && st == EPIC_OK; ++r) {
+    cudaEventRecord(e0, p->stream);
+    st = epic_image(p, d_volt, n_time, d_image, 0);
+    cudaEventRecord(e1, p->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "autotune timing");
+      break;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms.push_back(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EPIC_OK) return st;
+  std::sort(ms.begin(), ms.end());
+  *ms_out = ms[ms.size() / 2];
+  return EPIC_OK;
+}
+
+}  // namespace
+
+epic_status epic_autotune(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
+                          epic_tune_result* out) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad autotune arguments");
+  const bool cal = p->cal;
+  const long long frames = p->frames;
+  p->cal = false;                         // tuning runs must not touch the EPICal sums
+  epic_tune_result r{};
+  r.path = p->path;
+  double best = 0.0;
+  epic_status st = EPIC_OK;
+  const int reps = 3;
+  if (p->path == EPIC_PATH_FUSED) {
+    const int def = p->tune_units;
+    st = time_image(p, d_volt, n_time, d_image, reps, &r.ms_default);
+    best = r.ms_default;
+    r.units_target = def;
+    const int cand[] = {1, 2, 4, 8, 16, 32};
+    for (int k : cand) {
+      if (st != EPIC_OK) break;
+      p->tune_units = k;
+      double ms = 0;
+      st = time_image(p, d_volt, n_time, d_image, reps, &ms);
+      ++r.candidates;
+      if (st == EPIC_OK && ms < best) {
+        best = ms;
+        r.units_target = k;
+      }
+    }
+    p->tune_units = r.units_target;
+  } else {
+    const int def_nt = p->tune_nt, def_cols = p->tune_cols;
+    st = time_image(p, d_volt, n_time, d_image, reps, &r.ms_default);
+    best = r.ms_default;
+    r.batch_time = p->ws_time;
+    r.cols_target = def_cols;
+    const int budget_nt = p->ws_time;     // largest batch the scratch budget allows
+    for (int nt = 1; nt <= budget_nt && st == EPIC_OK; nt *= 2) {
+      for (int ct : {2, 4, 8}) {
+        p->tune_nt = nt;
+        p->tune_cols = ct;
+        double ms = 0;
+        st = time_image(p, d_volt, n_time, d_image, reps, &ms);
+        ++r.candidates;
+        if (st != EPIC_OK) break;
+        if (ms < best) {
+          best = ms;
+          r.batch_time = nt;
+          r.cols_target = ct;
+        }
+      }
+    }
+    if (r.batch_time == budget_nt && def_nt == 0) r.batch_time = 0;
+    p->tune_nt = r.batch_time;
+    p->tune_cols = r.cols_target;
+  }
+  p->cal = cal;
+  p->frames = frames;
+  r.ms_best = best;
+  if (out) *out = r;
+  return st;
+}
+
+epic_status epic_graph_capture(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
+                               double* d_gains_out) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad capture arguments");
+  if (!p->stream) return fail(EPIC_ERR_INVALID_ARG, "graph capture needs a non-default plan stream");
+  if (p->cal && p->frames != 0)
+    return fail(EPIC_ERR_STATE, "update EPICal before capturing (frames are pending)");
+  if (p->path == EPIC_PATH_UNFUSED) {
+    // allocate the batch scratch outside the capture
+    const bool cal = p->cal;
+    const long long frames = p->frames;
+    p->cal = false;
+    epic_status st = epic_image(p, d_volt, n_time, d_image, 0);
+    p->cal = cal;
+    p->frames = frames;
+    if (st) return st;
+  }
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  if (p->graph_exec) {
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  if (p->graph) {
+    cudaGraphDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  const long long frames_before = p->frames;
+  EPIC_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  epic_status st = epic_image(p, d_volt, n_time, d_image, 0);
+  if (st == EPIC_OK && p->cal) st = epical_update(p, d_gains_out, nullptr);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  p->frames = frames_before;               // replays account for their own frames
+  if (p->cal && st == EPIC_OK) p->iteration -= 1;
+  if (st != EPIC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  p->graph = g;
+  return EPIC_OK;
+}
+
+epic_status epic_graph_launch(epic_plan_t p) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!p->graph_exec) return fail(EPIC_ERR_STATE, "no captured graph");
+  EPIC_CUDA(cudaGraphLaunch(p->graph_exec, p->stream));
+  if (p->cal) p->iteration += 1;
+  return EPIC_OK;
+}
+
 epic_status epic_set_gains_device(epic_plan_t p, const double* d_gains) {
   if (epic_status s = check_plan(p)) return s;
   if (!d_gains) return fail(EPIC_ERR_INVALID_ARG, "d_gains is NULL");
@@ -808,7 +971,7 @@ epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_t
   a.dldi = d_dl_di;
   a.dldw = p->d_dldw.p;
   a.img_scale = 1.0 / static_cast<double>(n_time);
-  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
   a.rows_alloc = p->rows_alloc;
   a.rs = p->rs;
   const long long units = static_cast<long long>(p->nc) * a.segs;
@@ -865,7 +1028,7 @@ int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, dou
   a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
   a.kacc = p->d_kacc.p;
   a.pacc = p->d_pacc.p;
-  a.segs = choose_segments(p->nc, n_time, p->ctas);
+  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
   a.rows_alloc = p->rows_alloc;
   a.rs = p->rs;
   const long long units = static_cast<long long>(p->nc) * a.segs;

@@ -211,7 +211,7 @@ cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms
   constexpr int CBLK = (N + GROUPS - 1) / GROUPS;
   const int base_units = a.n_chan * CBLK;
   int segs = 1;
-  while (base_units * segs < 4 * sms && segs * 8 <= nt) segs *= 2;
+  while (base_units * segs < a.cols_target * sms && segs * 8 <= nt) segs *= 2;
   const int units = base_units * segs;
   const int cb = units < sms * 4 ? units : sms * 4;
   cols_fft_kernel<N><<<cb, kUBT, 0, s>>>(a, nt, segs);
