@@ -57,7 +57,7 @@ class Plan:
 
     def __init__(self, ant_xy_m, freq_hz, grid_n, cell=0.5, kernel="gaussian", support=3,
                  param=0.5, input="ci4", voltage_scale=None, flags=None, stream=None,
-                 path="auto", workspace_bytes=0):
+                 path="auto", workspace_bytes=0, precision="fp32"):
         lib = B.load()
         self._lib = lib
         self.ant = _f64(ant_xy_m).reshape(-1, 2)
@@ -82,7 +82,8 @@ class Plan:
         d.input = _INPUTS[input]
         d.voltage_scale = None if self._vs is None else self._vs.ctypes.data_as(B.c_fp)
         d.flags = None if self._fl is None else self._fl.ctypes.data_as(B.c_u8p)
-        d.precision = B.EPIC_PREC_FP32
+        d.precision = {"fp32": B.EPIC_PREC_FP32, "fp16": B.EPIC_PREC_FP16,
+                       "bf16": B.EPIC_PREC_BF16}[precision]
         d.cuda_stream = ct.c_void_p(int(stream))
         d.path = _PATHS[path]
         d.workspace_bytes = int(workspace_bytes)

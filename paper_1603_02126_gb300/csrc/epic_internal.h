@@ -116,6 +116,25 @@ struct UnfusedArgs {
   int cols_target;         // column-FFT work units per SM to aim for
 };
 bool unfused_supported(int n);
+cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
+cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s);
+
+// Reduced-precision (tensor-core column DFT) batch, epic_tc.cu.
+struct TcArgs {
+  UnfusedArgs u;           // gridding inputs, grid scratch, image, pixel, EPICal sums
+  void* hh;                // [C*N][tb_cap][kp] FP16/BF16 scaled row spectra
+  float* fscale;           // [tb_cap*C] per-frame bound S_f
+  int tb_cap, kp, bf16;
+  int* err;                // device flag: a bounded wait timed out
+};
+bool tc_supported(int n, int rows_alloc);
+int tc_kp(int rows_alloc);
+size_t tc_smem(int kp);
+cudaError_t tc_prepare(bool bf16, size_t smem);
+bool tc_make_maps(void* dft, void* hh, int n, int n_chan, int tb_cap, int kp, bool bf16, void* tm_dft,
+                  void* tm_data);
+cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_data, long long t0, int nt,
+                            int sms, cudaStream_t s);
 // Enqueue the four kernels of one batch of nt time samples starting at t0.
 cudaError_t launch_unfused_batch(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
 

@@ -125,6 +125,19 @@ struct epic_plan_s {
   int tune_cols = 4;            // unfused: column units per SM to aim for
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+
+  // reduced-precision form (tensor-core column DFT)
+  int precision = EPIC_PREC_FP32;
+  int kp = 0;                   // K extent of the DFT (2 x window rows, padded to 64)
+  int tc_time = 0;              // time samples per batch
+  DevBuf<float2> d_tc_grid;     // [tc_time*C][rows_alloc][N]
+  DevBuf<uint16_t> d_tc_hh;     // [C*N][tc_time][kp]
+  DevBuf<uint16_t> d_tc_dft;    // [2N][kp]
+  DevBuf<float> d_tc_scale;     // [tc_time*C]
+  DevBuf<float2> d_tc_pix;      // [tc_time*C]
+  DevBuf<int> d_err;            // bounded-wait timeout flag
+  alignas(64) unsigned char tm_dft[128];
+  alignas(64) unsigned char tm_data[128];
 };
 
 namespace {
@@ -206,6 +219,120 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   return EPIC_OK;
 }
 
+// float -> IEEE binary16 / bfloat16 bits, round to nearest even (host).
+uint16_t to_half_bits(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  const int e = static_cast<int>((x >> 23) & 0xff) - 127 + 15;
+  uint32_t m = x & 0x7fffffu;
+  if (e >= 31) return static_cast<uint16_t>(sign | 0x7c00u);
+  if (e <= 0) {
+    if (e < -10) return static_cast<uint16_t>(sign);
+    m |= 0x800000u;
+    const int sh = 14 - e;
+    uint32_t v = m >> sh;
+    const uint32_t rem = m & ((1u << sh) - 1), half = 1u << (sh - 1);
+    if (rem > half || (rem == half && (v & 1))) ++v;
+    return static_cast<uint16_t>(sign | v);
+  }
+  uint32_t v = (static_cast<uint32_t>(e) << 10) | (m >> 13);
+  const uint32_t rem = m & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (v & 1))) ++v;
+  return static_cast<uint16_t>(sign | v);
+}
+
+uint16_t to_bf16_bits(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t lsb = (x >> 16) & 1u;
+  x += 0x7fffu + lsb;
+  return static_cast<uint16_t>(x >> 16);
+}
+
+// Reduced-precision form: FP32 gridding and row FFTs, FP16/BF16 tensor-core
+// column DFT with per-frame power-of-two scaling, FP64 image accumulation.
+epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double* d_image) {
+  const int C = p->nc, N = p->n;
+  if (p->tc_time == 0) {
+    const size_t per_t = static_cast<size_t>(C) *
+                         (static_cast<size_t>(p->rows_alloc) * N * sizeof(float2) +
+                          static_cast<size_t>(N) * p->kp * 2 + sizeof(float) + sizeof(float2));
+    long long nt = static_cast<long long>(p->workspace_budget / per_t);
+    nt = std::max<long long>(1, std::min<long long>(nt, 128));
+    const size_t n_grid = static_cast<size_t>(nt) * C * p->rows_alloc * N;
+    const size_t n_hh = static_cast<size_t>(C) * N * nt * p->kp;
+    cudaError_t es[] = {p->d_tc_grid.alloc(n_grid), p->d_tc_hh.alloc(n_hh),
+                        p->d_tc_dft.alloc(static_cast<size_t>(2) * N * p->kp),
+                        p->d_tc_scale.alloc(static_cast<size_t>(nt) * C),
+                        p->d_tc_pix.alloc(static_cast<size_t>(nt) * C)};
+    for (cudaError_t x : es)
+      if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "tensor-path scratch allocation failed");
+    EPIC_CUDA(cudaMemset(p->d_tc_hh.p, 0, n_hh * 2));
+    // real-expanded DFT over window rows: rows 2 ky + (re, im), columns 2 jw + (re, im)
+    const bool bf = p->precision == EPIC_PREC_BF16;
+    std::vector<uint16_t> dft(static_cast<size_t>(2) * N * p->kp);
+    for (int ky = 0; ky < N; ++ky)
+      for (int jw = 0; jw < p->kp / 2; ++jw) {
+        const long long m = (static_cast<long long>(jw) * ky) % N;
+        const double th = 2.0 * kPi * static_cast<double>(m) / N;
+        const float cs = static_cast<float>(std::cos(th)), sn = static_cast<float>(std::sin(th));
+        auto put = [&](int r, int k, float v) {
+          dft[static_cast<size_t>(r) * p->kp + k] = bf ? to_bf16_bits(v) : to_half_bits(v);
+        };
+        put(2 * ky, 2 * jw, cs);
+        put(2 * ky, 2 * jw + 1, -sn);
+        put(2 * ky + 1, 2 * jw, sn);
+        put(2 * ky + 1, 2 * jw + 1, cs);
+      }
+    EPIC_CUDA(cudaMemcpy(p->d_tc_dft.p, dft.data(), dft.size() * 2, cudaMemcpyHostToDevice));
+    if (!epic::tc_make_maps(p->d_tc_dft.p, p->d_tc_hh.p, N, C, static_cast<int>(nt), p->kp, bf, p->tm_dft,
+                            p->tm_data))
+      return fail(EPIC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    p->tc_time = static_cast<int>(nt);
+  }
+  epic::TcArgs a{};
+  epic::UnfusedArgs& u = a.u;
+  u.volt = d_volt;
+  u.input_fmt = p->input;
+  u.n_chan = C;
+  u.n_ant = p->na;
+  u.support = p->k;
+  u.grid_n = N;
+  u.cell0 = p->d_cell0.p;
+  u.wts = p->d_wts.p;
+  u.wgain = p->d_wgain.p;
+  u.vscale = p->d_vscale.p;
+  u.win = p->d_win.p;
+  u.twid = p->d_twid.p;
+  u.grid = p->d_tc_grid.p;
+  u.spec = nullptr;
+  u.pix = p->d_tc_pix.p;
+  u.rows_alloc = p->rows_alloc;
+  u.rs = p->rs;
+  u.image = d_image;
+  u.img_scale = 1.0 / static_cast<double>(n_time);
+  u.do_cal = p->cal ? 1 : 0;
+  u.k0x = p->cal ? p->k0x : 0;
+  u.k0y = p->cal ? p->k0y : 0;
+  u.pix_sign = ((u.k0x + u.k0y) & 1) ? -1.0f : 1.0f;
+  u.kacc = p->d_kacc.p;
+  u.pacc = p->d_pacc.p;
+  u.cols_target = p->tune_cols;
+  a.hh = p->d_tc_hh.p;
+  a.fscale = p->d_tc_scale.p;
+  a.tb_cap = p->tc_time;
+  a.kp = p->kp;
+  a.bf16 = p->precision == EPIC_PREC_BF16 ? 1 : 0;
+  a.err = p->d_err.p;
+  for (long long t0 = 0; t0 < n_time; t0 += p->tc_time) {
+    const int n = static_cast<int>(std::min<long long>(p->tc_time, n_time - t0));
+    EPIC_CUDA(epic::launch_tc_batch(a, p->tm_dft, p->tm_data, t0, n, p->sms, p->stream));
+  }
+  if (p->cal) p->frames += n_time;
+  return EPIC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -229,8 +356,10 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     return fail(EPIC_ERR_INVALID_ARG, "kernel_param must be > 0");
   if (d->input != EPIC_IN_CI4 && d->input != EPIC_IN_COMPLEX64)
     return fail(EPIC_ERR_INVALID_ARG, "unknown input format");
-  if (d->precision != EPIC_PREC_FP32)
-    return fail(EPIC_ERR_UNSUPPORTED, "only EPIC_PREC_FP32 is built");
+  if (d->precision != EPIC_PREC_FP32 && d->precision != EPIC_PREC_FP16 && d->precision != EPIC_PREC_BF16)
+    return fail(EPIC_ERR_INVALID_ARG, "unknown precision");
+  if (d->precision != EPIC_PREC_FP32 && d->path == EPIC_PATH_FUSED)
+    return fail(EPIC_ERR_UNSUPPORTED, "FP16/BF16 run on the tensor-core column DFT (not the fused path)");
   for (int c = 0; c < d->n_chan; ++c)
     if (!(d->freq_hz[c] > 0) || !std::isfinite(d->freq_hz[c]))
       return fail(EPIC_ERR_INVALID_ARG, "frequencies must be finite and > 0");
@@ -366,7 +495,21 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
-  bool fused = fused_shape && d->path != EPIC_PATH_UNFUSED;
+  bool fused = fused_shape && d->path != EPIC_PATH_UNFUSED && d->precision == EPIC_PREC_FP32;
+  p->precision = d->precision;
+  if (p->precision != EPIC_PREC_FP32) {
+    if (!epic::tc_supported(N, p->rows_alloc)) {
+      delete p;
+      return fail(EPIC_ERR_UNSUPPORTED, "FP16/BF16 form: grid_n must be 128 or 256 and the array "
+                                        "footprint at most 128 grid rows");
+    }
+    p->kp = epic::tc_kp(p->rows_alloc);
+    e = epic::tc_prepare(p->precision == EPIC_PREC_BF16, epic::tc_smem(p->kp));
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "tensor-core kernel attributes");
+    }
+  }
   if (fused) {
     p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs);
     if (p->smem > static_cast<size_t>(smem_optin)) {
@@ -422,6 +565,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
   e = p->d_held.alloc(1);
   if (e == cudaSuccess) e = cudaMemset(p->d_held.p, 0, sizeof(int));
+  if (e == cudaSuccess) e = p->d_err.alloc(1);
+  if (e == cudaSuccess) e = cudaMemset(p->d_err.p, 0, sizeof(int));
   if (e != cudaSuccess) {
     epic_plan_destroy(p);
     return cuda_fail(e, "counter");
@@ -450,6 +595,12 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_stage_img.release();
   p->d_ws.release();
   p->d_dldw.release();
+  p->d_tc_grid.release();
+  p->d_tc_hh.release();
+  p->d_tc_dft.release();
+  p->d_tc_scale.release();
+  p->d_tc_pix.release();
+  p->d_err.release();
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   delete p;
@@ -509,6 +660,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
   const size_t img_bytes = static_cast<size_t>(p->nc) * p->n * p->n * sizeof(double);
   if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_image, 0, img_bytes, p->stream));
+  if (p->precision != EPIC_PREC_FP32) return image_tc(p, d_volt, n_time, d_image);
   if (p->path == EPIC_PATH_UNFUSED) return image_unfused(p, d_volt, n_time, d_image);
   epic::ImageArgs a{};
   a.volt = d_volt;
@@ -688,10 +840,15 @@ epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
 epic_status epic_plan_sync(epic_plan_t p, int* n_held) {
   if (epic_status s = check_plan(p)) return s;
   EPIC_CUDA(cudaStreamSynchronize(p->stream));
-  int held = 0;
+  int held = 0, err = 0;
   EPIC_CUDA(cudaMemcpy(&held, p->d_held.p, sizeof(int), cudaMemcpyDeviceToHost));
   EPIC_CUDA(cudaMemset(p->d_held.p, 0, sizeof(int)));
+  EPIC_CUDA(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (n_held) *n_held = held;
+  if (err) {
+    EPIC_CUDA(cudaMemset(p->d_err.p, 0, sizeof(int)));
+    return fail(EPIC_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core kernel)");
+  }
   if (held > 0) return fail(EPIC_ERR_NUMERIC, std::to_string(held) + " gains held by the EPICal update");
   return EPIC_OK;
 }

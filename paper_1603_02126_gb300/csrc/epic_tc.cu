@@ -1,0 +1,505 @@
+// Reduced-precision EPIC imaging: the column transform of Eq. 10 as a
+// tensor-core GEMM (tcgen05, FP16 or BF16 operands, FP32 accumulation).
+//
+// Per batch of frames (frame f = t_local * C + c), after the FP32 gridding of
+// the plain path:
+//   frame_scale  S_f = sum_a |w_a E_a| / Na, an upper bound of every row
+//                spectrum value; s_f = largest power of two with s_f S_f < 1;
+//   rows_lp      FP32 N-point FFT of each occupied grid row; the spectrum is
+//                scaled by s_f, rounded to FP16/BF16 and stored K-major as
+//                Hh[c][kx][t][2 jw + (re, im)]; the calibrator pixel is
+//                summed in FP32 from the same spectra;
+//   tc_cols      D[r][t] = sum_k' F[r][k'] Hh[c][kx][t][k'] with the
+//                real-expanded DFT matrix F (rows r = 2 ky + (re, im),
+//                columns k' = 2 jw + (re, im)); TMEM lane r then sums
+//                D[r][t]^2 / s_t^2 over the frames t of the tile, lanes 2ky and
+//                2ky+1 are added and the result goes to image[c][ky][kx]
+//                (FP64 atomics).  |E|^2 does not depend on where the window
+//                starts, so F uses window rows jw.
+// tc_cols is a persistent, warp-specialised kernel: warp 0 issues TMA loads
+// (128B-swizzled, 2-stage ring of data tiles; the CTA's DFT tile is loaded
+// once), warp 1 owns the TMEM allocation and issues tcgen05.mma from one
+// thread (M = 128 DFT rows, N = 128 frames, K = 16 per instruction), warps
+// 2-5 drain the double-buffered TMEM accumulators.  Every mbarrier wait is
+// bounded; on timeout the kernel records an error flag and winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "epic_fft.cuh"
+#include "epic_internal.h"
+
+namespace epic {
+namespace {
+
+template <int N> struct LCfg;
+template <> struct LCfg<128> { static constexpr int N1 = 8,  N2 = 16; };
+template <> struct LCfg<256> { static constexpr int N1 = 16, N2 = 16; };
+
+constexpr int kLBT = 256;
+
+// Largest power of two s with s * S < 1 (S > 0), from the float's exponent.
+__device__ __forceinline__ float pow2_below_inverse(float S) {
+  if (!(S > 0.f)) return 1.0f;
+  const int e = static_cast<int>((__float_as_uint(S) >> 23) & 0xff) - 127;
+  int k = -(e + 1);
+  k = k < -126 ? -126 : (k > 127 ? 127 : k);
+  return __uint_as_float(static_cast<unsigned>(k + 127) << 23);
+}
+
+__device__ __forceinline__ float2 load_volt_tc(const void* volt, int fmt, size_t idx) {
+  if (fmt == 0) {
+    const unsigned b = __ldg(static_cast<const unsigned char*>(volt) + idx);
+    const int re = static_cast<int>(b << 24) >> 28;
+    const int im = static_cast<int>(b << 28) >> 28;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+  return __ldg(static_cast<const float2*>(volt) + idx);
+}
+
+template <typename T> __device__ __forceinline__ T to_lp(float x);
+template <> __device__ __forceinline__ __half to_lp<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// ---- S_f: one warp per frame ----
+__global__ void frame_scale_kernel(const TcArgs A, long long t0, int nt) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int C = A.u.n_chan, Na = A.u.n_ant;
+  if (warp >= nt * C) return;
+  const int c = warp % C, tl = warp / C;
+  const float vs = A.u.vscale ? __ldg(A.u.vscale + c) : 1.0f;
+  float s = 0.f;
+  for (int a = lane; a < Na; a += 32) {
+    if (__ldg(A.u.cell0 + static_cast<size_t>(c) * Na + a) < 0) continue;
+    const float2 e = load_volt_tc(A.u.volt, A.u.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
+    const float2 w = __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a);
+    const float2 ec = fft::cmul(make_float2(e.x * vs, e.y * vs), w);
+    s += sqrtf(ec.x * ec.x + ec.y * ec.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(fft::kFull, s, o);
+  if (lane == 0) A.fscale[warp] = s / static_cast<float>(Na);
+}
+
+// ---- FP32 row FFTs, low-precision K-major output, FP32 calibrator pixel ----
+template <int N, typename T>
+__global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, int nt) {
+  constexpr int N1 = LCfg<N>::N1, N2 = LCfg<N>::N2, H = N2 / N1;
+  constexpr int GROUPS = kLBT / N1;
+  using X = fft::Xchg<N1, N2>;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[GROUPS * X::ZG];
+  for (int i = threadIdx.x; i < N; i += kLBT) tw[i] = A.u.twid[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
+  const unsigned gmask = fft::group_mask<N1>(lane);
+  float2* z = zbuf + g * X::ZG;
+  const int C = A.u.n_chan;
+  const int ra = A.u.rows_alloc;
+  const long long pairs = static_cast<long long>(nt) * C * ra;
+  const int pn1 = A.u.k0x % N1, pq = A.u.k0x / N1;
+  const int pslot = (pq % H) * N1 + pq / H;
+  T* hh = static_cast<T*>(A.hh);
+  for (long long pr = static_cast<long long>(blockIdx.x) * GROUPS + g; pr < pairs;
+       pr += static_cast<long long>(gridDim.x) * GROUPS) {
+    const int row = static_cast<int>(pr % ra);
+    const long long f = pr / ra;
+    const int c = static_cast<int>(f % C);
+    const int tl = static_cast<int>(f / C);
+    const int2 wn = __ldg(A.u.win + c);
+    if (row >= wn.y) continue;                      // group-uniform
+    const float2* src = A.u.grid + (static_cast<size_t>(f) * ra + row) * N;
+    float2 v[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) v[j] = src[n1 + N1 * j];
+    fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
+    const float s = pow2_below_inverse(__ldg(A.fscale + f));
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int kx = n1 + N1 * h + N2 * k1;
+        const float2 x = v[h * N1 + k1];
+        T* dst = hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * row;
+        dst[0] = to_lp<T>(x.x * s);
+        dst[1] = to_lp<T>(x.y * s);
+      }
+    if (A.u.do_cal && n1 == pn1) {
+      // pixel (k0x, k0y): sum over rows of X[jy][k0x] e^{+2 pi i jy k0y / N}
+      float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < N2; ++q)
+        if (q == pslot) x = v[q];
+      const int jy = wn.x + row;
+      const float2 t = tw[(jy * A.u.k0y) & (N - 1)];
+      const float2 y = fft::cmul(x, t);
+      atomicAdd(&A.u.pix[f].x, y.x * A.u.pix_sign);
+      atomicAdd(&A.u.pix[f].y, y.y * A.u.pix_sign);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA / mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO); the leading offset is unused in this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(16 >> 4) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTcThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTile = 128;               // DFT rows and frames per tile
+constexpr int kChunkBytes = kTile * 128; // one 64-element K chunk of a 128-row tile
+constexpr uint32_t kTmemCols = 256;      // two 128-column accumulators
+
+// Dynamic shared memory of tc_cols_kernel for a K extent of kp elements.
+size_t tc_smem_bytes(int kp) {
+  const size_t tile = static_cast<size_t>(kp / 64) * kChunkBytes;
+  return 1024 /*alignment slack*/ + 3 * tile + 256 /*barriers*/;
+}
+
+template <bool kBf16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_cols_kernel(const __grid_constant__ CUtensorMap tm_dft, const __grid_constant__ CUtensorMap tm_data,
+                   const TcArgs A, int nt) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int kc_n = A.kp / 64;
+  const uint32_t tile_bytes = static_cast<uint32_t>(kc_n) * kChunkBytes;
+  unsigned char* sA = base;                         // DFT tile (resident)
+  unsigned char* sD = base + tile_bytes;            // 2 data stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 3 * tile_bytes);
+  // bars: 0,1 full; 2,3 empty; 4,5 tmem_full; 6,7 tmem_empty; 8 dft_full
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = A.u.n_chan, N = A.u.grid_n;
+  const int MB = 2 * N / kTile;
+  const int tbk = (nt + kTile - 1) / kTile;
+  const long long tiles = static_cast<long long>(MB) * C * N * tbk;
+  const int G = gridDim.x;                          // multiple of MB
+  const int mb = blockIdx.x % MB;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(bars + i), 1);
+      mbar_init(smem_u32(bars + 2 + i), 1);
+      mbar_init(smem_u32(bars + 4 + i), 1);
+      mbar_init(smem_u32(bars + 6 + i), 4);
+    }
+    mbar_init(smem_u32(bars + 8), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_dft)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_data)) : "memory");
+      const uint32_t bdft = smem_u32(bars + 8);
+      mbar_expect_tx(bdft, tile_bytes);
+      for (int kc = 0; kc < kc_n; ++kc)
+        tma_load_2d(smem_u32(sA + kc * kChunkBytes), &tm_dft, kc * 64, mb * kTile, bdft);
+      int i = 0;
+      for (long long u = blockIdx.x; u < tiles; u += G, ++i) {
+        const int s = i & 1;
+        const uint32_t ph = (i >> 1) & 1;
+        if (!mbar_wait(smem_u32(bars + 2 + s), ph ^ 1, abort_flag, A.err)) break;
+        const long long rest = u / MB;
+        const int tb = static_cast<int>(rest % tbk);
+        const long long ck = rest / tbk;             // c * N + kx
+        const uint32_t bfull = smem_u32(bars + s);
+        mbar_expect_tx(bfull, tile_bytes);
+        for (int kc = 0; kc < kc_n; ++kc)
+          tma_load_3d(smem_u32(sD + s * tile_bytes + kc * kChunkBytes), &tm_data, kc * 64, tb * kTile,
+                      static_cast<int>(ck), bfull);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((kBf16 ? 1u : 0u) << 7) | ((kBf16 ? 1u : 0u) << 10) |
+                             (static_cast<uint32_t>(kTile >> 3) << 17) |
+                             (static_cast<uint32_t>(kTile >> 4) << 24);
+      bool ok = mbar_wait(smem_u32(bars + 8), 0, abort_flag, A.err);
+      int i = 0;
+      for (long long u = blockIdx.x; ok && u < tiles; u += G, ++i) {
+        const int s = i & 1, acc = i & 1;
+        const uint32_t ph = (i >> 1) & 1;
+        if (!mbar_wait(smem_u32(bars + 6 + acc), ph ^ 1, abort_flag, A.err)) break;
+        tc_fence_after();
+        if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sD + s * tile_bytes);
+        for (int kc = 0; kc < kc_n; ++kc)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t off = kc * kChunkBytes + k * 32;
+            mma_f16(d_tmem, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, (kc | k) != 0);
+          }
+        mma_commit(smem_u32(bars + 2 + s));   // data stage free once these MMAs finish
+        mma_commit(smem_u32(bars + 4 + acc)); // accumulator ready
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2-5) ----------------
+    const int q = warp & 3;                        // TMEM lane quarter of this warp
+    const int r = mb * kTile + q * 32 + lane;      // DFT row = 2 ky + (re, im)
+    const int ky = r >> 1;
+    int i = 0;
+    for (long long u = blockIdx.x; u < tiles; u += G, ++i) {
+      const int acc = i & 1;
+      const uint32_t ph = (i >> 1) & 1;
+      if (!mbar_wait(smem_u32(bars + 4 + acc), ph, abort_flag, A.err)) break;
+      tc_fence_after();
+      const long long rest = u / MB;
+      const int tb = static_cast<int>(rest % tbk);
+      const long long ck = rest / tbk;
+      const int c = static_cast<int>(ck / N), kx = static_cast<int>(ck % N);
+      float sum = 0.f;
+#pragma unroll 1
+      for (int ch = 0; ch < kTile / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32),
+                  v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int t = tb * kTile + ch * 32 + j;
+          float w = 0.f;
+          if (t < nt) {
+            const float s = pow2_below_inverse(__ldg(A.fscale + static_cast<size_t>(t) * C + c));
+            const float inv = 1.0f / s;            // exact: s is a power of two
+            w = inv * inv;
+          }
+          sum += v[j] * v[j] * w;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(bars + 6 + acc));
+      const float other = __shfl_xor_sync(fft::kFull, sum, 1);
+      if ((lane & 1) == 0)
+        atomicAdd(A.u.image + (static_cast<size_t>(c) * N + ky) * N + kx,
+                  static_cast<double>(sum + other) * A.u.img_scale);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <int N, typename T>
+cudaError_t rows_lp_n(const TcArgs& a, int nt, int sms, cudaStream_t s) {
+  constexpr int GROUPS = kLBT / LCfg<N>::N1;
+  const long long pairs = static_cast<long long>(nt) * a.u.n_chan * a.u.rows_alloc;
+  long long rb = (pairs + GROUPS - 1) / GROUPS;
+  if (rb > static_cast<long long>(sms) * 8) rb = static_cast<long long>(sms) * 8;
+  rows_lp_kernel<N, T><<<static_cast<unsigned>(rb), kLBT, 0, s>>>(a, nt);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported(int n, int rows_alloc) { return (n == 128 || n == 256) && 2 * rows_alloc <= 256; }
+
+int tc_kp(int rows_alloc) { return ((2 * rows_alloc + 63) / 64) * 64; }
+
+size_t tc_smem(int kp) { return tc_smem_bytes(kp); }
+
+cudaError_t tc_prepare(bool bf16, size_t smem) {
+  if (bf16)
+    return cudaFuncSetAttribute(tc_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem));
+  return cudaFuncSetAttribute(tc_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem));
+}
+
+cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_data, long long t0, int nt,
+                            int sms, cudaStream_t s) {
+  const size_t gbytes = static_cast<size_t>(nt) * a.u.n_chan * a.u.rows_alloc * a.u.grid_n * sizeof(float2);
+  cudaError_t e = cudaMemsetAsync(a.u.grid, 0, gbytes, s);
+  if (e == cudaSuccess && a.u.do_cal)
+    e = cudaMemsetAsync(a.u.pix, 0, static_cast<size_t>(nt) * a.u.n_chan * sizeof(float2), s);
+  if (e != cudaSuccess) return e;
+  e = launch_grid_scatter(a.u, t0, nt, sms, s);
+  if (e != cudaSuccess) return e;
+  const int frames = nt * a.u.n_chan;
+  frame_scale_kernel<<<(frames * 32 + 255) / 256, 256, 0, s>>>(a, t0, nt);
+  if (a.bf16) e = (a.u.grid_n == 128) ? rows_lp_n<128, __nv_bfloat16>(a, nt, sms, s)
+                                      : rows_lp_n<256, __nv_bfloat16>(a, nt, sms, s);
+  else e = (a.u.grid_n == 128) ? rows_lp_n<128, __half>(a, nt, sms, s) : rows_lp_n<256, __half>(a, nt, sms, s);
+  if (e != cudaSuccess) return e;
+  const int MB = 2 * a.u.grid_n / kTile;
+  const int grid = (sms / MB) * MB;
+  const size_t smem = tc_smem_bytes(a.kp);
+  const CUtensorMap* td = static_cast<const CUtensorMap*>(tm_dft);
+  const CUtensorMap* tt = static_cast<const CUtensorMap*>(tm_data);
+  if (a.bf16) tc_cols_kernel<true><<<grid, kTcThreads, smem, s>>>(*td, *tt, a, nt);
+  else tc_cols_kernel<false><<<grid, kTcThreads, smem, s>>>(*td, *tt, a, nt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.u.do_cal) e = launch_correlate(a.u, t0, nt, s);
+  return e;
+}
+
+// Tensor maps over the DFT matrix [2N][kp] and the spectra [C*N][tb_cap][kp].
+bool tc_make_maps(void* dft, void* hh, int n, int n_chan, int tb_cap, int kp, bool bf16, void* tm_dft,
+                  void* tm_data) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(2 * n)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(kp) * 2};
+    cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kTile)};
+    cuuint32_t es[2] = {1, 1};
+    if (encode(static_cast<CUtensorMap*>(tm_dft), dt, 2, dft, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(tb_cap),
+                          static_cast<cuuint64_t>(n_chan) * n};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2, static_cast<cuuint64_t>(kp) * 2 * tb_cap};
+    cuuint32_t box[3] = {64, static_cast<cuuint32_t>(kTile), 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (encode(static_cast<CUtensorMap*>(tm_data), dt, 3, hh, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+}  // namespace epic

@@ -226,6 +226,20 @@ cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms
 
 bool unfused_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
 
+cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
+  const long long items = static_cast<long long>(nt) * a.n_chan * a.support * a.n_ant;
+  long long gb = (items + 255) / 256;
+  if (gb > static_cast<long long>(sms) * 16) gb = static_cast<long long>(sms) * 16;
+  grid_scatter_kernel<<<static_cast<unsigned>(gb), 256, 0, s>>>(a, t0, nt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s) {
+  const int n = a.n_chan * a.n_ant;
+  correlate_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, t0, nt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unfused_batch(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
   switch (a.grid_n) {
     case 32: return launch_unfused_n<32>(a, t0, nt, sms, s);

@@ -73,7 +73,8 @@ def _desc(B, **over):
     (dict(kernel_param=-1.0), 1),
     (dict(cell_wavelengths=0.0), 1),
     (dict(input=7), 1),
-    (dict(precision=1), 7),
+    (dict(precision=5), 1),
+    (dict(precision=1, path=1), 7),
     (dict(grid_n=1024), 7),
     (dict(ant=[[60.0, 0.0], [0.0, 0.0]]), 2),
 ])
