@@ -152,6 +152,189 @@ def cpu_baseline(w, volt_cpu, budget_s=15.0):
                       f"(image + EPICal correlation and update, FP64 NumPy), {dt:.1f} s"}
 
 
+def _timer(torch, flush, stream):
+    """Median CUDA-event time (ms) of fn() over reps, L2 flushed before each."""
+    def run(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out))
+    return run
+
+
+def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
+    """The other forms of the hot path, each on its own workload, timed as
+    speedups over the plain FP32 form of the same workload."""
+    run = _timer(torch, flush, stream)
+    reps = max(3, min(steps, 5))
+    out = {}
+    sc = stream.cuda_stream
+    kw1 = dict(support=3, param=0.5, input="ci4", voltage_scale=w1["lsb"], stream=sc)
+    C1 = len(w1["freqs"])
+    img1 = torch.empty((C1, 128, 128), dtype=torch.float64, device=dev)
+
+    # -- LWA-like interval: plain unfused FP32 vs fused FP32 vs graph + autotune
+    pu = Plan(w1["ant_xy"], w1["freqs"], 128, 0.5, path="unfused", workspace_bytes=4 << 30, **kw1)
+    pu.configure((0.0, 0.0), w1["model"], w1["gamma"])
+    pf = Plan(w1["ant_xy"], w1["freqs"], 128, 0.5, path="fused", **kw1)
+    pf.configure((0.0, 0.0), w1["model"], w1["gamma"])
+    gout = torch.empty((C1, 256), dtype=torch.complex128, device=dev)
+    for p in (pu, pf):
+        p.image(volt1, img1)
+        p.update(gout)
+    ms_plain = run(lambda: (pu.image(volt1, img1), pu.update(gout)), reps)
+    ms_fused = run(lambda: (pf.image(volt1, img1), pf.update(gout)), reps)
+    info_u = pu.info()
+    rows = info_u["window_rows"]
+    # plain path bytes per frame: grid window written (memset) and re-read by
+    # the row FFTs, spectra written and read by the column FFTs, voltages twice
+    per_frame = 4 * rows * 128 * 8 + 2 * 256
+    plain_gbs = per_frame * C1 * w1["n_time"] / (ms_plain / 1e3) / 1e9
+    tune = pf.autotune(volt1, img1)
+    pf.graph_capture(volt1, img1, gout)
+    ms_graph = run(pf.graph_launch, reps)
+    frames1 = C1 * w1["n_time"]
+    out["lwa256_n128"] = {
+        "workload": "LWA-like interval, Na=256, C=64, N=128, T=10000 (as the headline)",
+        "plain_fp32_unfused": {"ms": ms_plain, "frames_per_s": frames1 / ms_plain * 1e3,
+                               "hbm_gbs": plain_gbs, "hbm_frac_of_measured": None},
+        "fused_fp32": {"ms": ms_fused, "frames_per_s": frames1 / ms_fused * 1e3,
+                       "speedup_vs_plain": ms_plain / ms_fused},
+        "batched_graph_autotuned": {"ms": ms_graph, "frames_per_s": frames1 / ms_graph * 1e3,
+                                    "speedup_vs_plain": ms_plain / ms_graph, "tune": tune},
+    }
+    pu.close()
+    pf.close()
+
+    # -- precision: Na=1024, C=32, N=256, T=4096 (4-bit), FP16/BF16 tensor cores vs plain FP32
+    w2 = synth.workload("compact1024")
+    v2 = synth.voltages_ci4_torch(w2["ant_xy"], w2["freqs"], w2["gains"], w2["sky"], w2["n_time"],
+                                  w2["noise_power"], w2["lsb"], seed=2, device=dev)
+    C2 = len(w2["freqs"])
+    img2 = torch.empty((C2, 256, 256), dtype=torch.float64, device=dev)
+    kw2 = dict(support=3, param=0.5, input="ci4", voltage_scale=w2["lsb"], stream=sc)
+    res2 = {"workload": "Na=1024 in a 200 m disc, C=32 ch 40-80 MHz, N=256, T=4096, 4-bit"}
+    ref_img = None
+    frames2 = C2 * w2["n_time"]
+    ms_p2 = None
+    for prec in ("fp32", "fp16", "bf16"):
+        p = Plan(w2["ant_xy"], w2["freqs"], 256, 0.5, path="unfused", precision=prec,
+                 workspace_bytes=4 << 30, **kw2)
+        p.image(v2, img2)
+        ms = run(lambda: p.image(v2, img2), reps)
+        p.image(v2, img2)
+        torch.cuda.synchronize()
+        img = img2.clone()
+        entry = {"ms": ms, "frames_per_s": frames2 / ms * 1e3}
+        if prec == "fp32":
+            ref_img = img
+            ms_p2 = ms
+        else:
+            entry["speedup_vs_plain_fp32"] = ms_p2 / ms
+            entry["image_rel_l2_vs_fp32"] = float(torch.linalg.norm(img - ref_img) /
+                                                  torch.linalg.norm(ref_img))
+        res2[prec] = entry
+        p.close()
+    out["compact1024_n256"] = res2
+    del v2, img2
+
+    # -- batching: Na=2048 hex, C=256, N=512, T=4096 (complex64), plain vs graph + autotune
+    w3 = synth.workload("hex2048")
+    v3 = synth.voltages_c64_torch(w3["ant_xy"], w3["freqs"], w3["gains"], w3["sky"], w3["n_time"],
+                                  w3["noise_power"], seed=3, device=dev)
+    C3 = len(w3["freqs"])
+    img3 = torch.empty((C3, 512, 512), dtype=torch.float64, device=dev)
+    g3 = torch.empty((C3, 2048), dtype=torch.complex128, device=dev)
+    kw3 = dict(support=3, param=0.5, input="c64", stream=sc)
+    frames3 = C3 * w3["n_time"]
+    p3 = Plan(w3["ant_xy"], w3["freqs"], 512, 0.5, path="unfused", workspace_bytes=2 << 30, **kw3)
+    p3.configure((0.0, 0.0), w3["model"], w3["gamma"])
+    p3.image(v3, img3)
+    p3.update(g3)
+    ms_p3 = run(lambda: (p3.image(v3, img3), p3.update(g3)), 2)
+    p3b = Plan(w3["ant_xy"], w3["freqs"], 512, 0.5, path="unfused", workspace_bytes=8 << 30, **kw3)
+    p3b.configure((0.0, 0.0), w3["model"], w3["gamma"])
+    tune3 = p3b.autotune(v3[:256], img3)
+    p3b.graph_capture(v3, img3, g3)
+    p3b.graph_launch()
+    ms_b3 = run(p3b.graph_launch, 2)
+    out["hex2048_n512"] = {
+        "workload": "Na=2048 hexagonal 8 m pitch +-0.5 m jitter, C=256 ch 50-100 MHz, N=512, "
+                    "T=4096 complex64, EPICal armed",
+        "plain_fp32": {"ms": ms_p3, "frames_per_s": frames3 / ms_p3 * 1e3},
+        "batched_graph_autotuned": {"ms": ms_b3, "frames_per_s": frames3 / ms_b3 * 1e3,
+                                    "speedup_vs_plain": ms_p3 / ms_b3, "tune": tune3},
+    }
+    p3.close()
+    p3b.close()
+    del v3, img3
+
+    # -- differentiation: Na=256, N=128, C=16, T=4096; chi^2 to the 50-source model image
+    from paper_1603_02126_gb300.autograd import EpicImageFn, chi2, solve_gains
+    w4 = synth.workload("lwa_diff")
+    v4 = synth.voltages_ci4_torch(w4["ant_xy"], w4["freqs"], w4["gains"], w4["sky"][:50],
+                                  w4["n_time"], w4["noise_power"], w4["lsb"], seed=4, device=dev)
+    C4 = len(w4["freqs"])
+    mf = torch.from_numpy(synth.model_frames_c64(w4["ant_xy"], w4["freqs"], w4["model"])).to(dev)
+    pm = Plan(w4["ant_xy"], w4["freqs"], 128, 0.5, input="c64", stream=sc)
+    M = pm.image(mf) * mf.shape[0]
+    pm.close()
+    p4 = Plan(w4["ant_xy"], w4["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+              voltage_scale=w4["lsb"], stream=sc)
+    g_true = torch.from_numpy(w4["gains"]).to(dev)
+
+    def fwd_bwd():
+        g = g_true.clone().requires_grad_(True)
+        chi2(EpicImageFn.apply(g, v4, p4), M).backward()
+
+    fwd_bwd()
+    ms_fb = run(fwd_bwd, reps)
+    ms_f = run(lambda: p4.image(v4), reps)
+    # gradient solve vs EPICal, both from gains within ~10 % / 0.2 rad of the truth
+    rng = np.random.default_rng(44)
+    pert = (1 + 0.1 * rng.normal(size=w4["gains"].shape)) * np.exp(0.2j * rng.normal(size=w4["gains"].shape))
+    g0 = torch.from_numpy(w4["gains"] * pert).to(dev)
+    t0 = time.perf_counter()
+    g_adam = solve_gains(p4, v4, M, g0, steps=60, lr=0.01, decay=0.97)
+    torch.cuda.synchronize()
+    adam_s = time.perf_counter() - t0
+    pe = Plan(w4["ant_xy"], w4["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+              voltage_scale=w4["lsb"], stream=sc)
+    pe.configure((0.0, 0.0), w4["model"], w4["gamma"], g0=w4["gains"] * pert)
+    t0 = time.perf_counter()
+    for _ in range(60):
+        pe.image(v4)
+        pe.update()
+    pe.sync()
+    epical_s = time.perf_counter() - t0
+
+    def sig(g):
+        """sigma_g (Eq. 22) after removing each channel's global phase."""
+        gt = w4["gains"]
+        ph = np.angle(np.sum(g * np.conj(gt), axis=1, keepdims=True))
+        ga = g * np.exp(-1j * ph)
+        return float(np.sqrt(np.mean(np.abs(ga - gt) ** 2 / np.abs(gt) ** 2)))
+
+    out["lwa_diff_n128"] = {
+        "workload": "Na=256 (LWA-like), N=128, C=16, T=4096, 4-bit; loss = chi^2 to the 50-source "
+                    "model image",
+        "forward_ms": ms_f, "forward_backward_ms": ms_fb,
+        "adam_60_steps": {"s": adam_s, "sigma_g": sig(g_adam.cpu().numpy())},
+        "epical_60_loops": {"s": epical_s, "sigma_g": sig(pe.gains())},
+        "sigma_g_start": sig(w4["gains"] * pert),
+    }
+    p4.close()
+    pe.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded samples."""
     if rank != 0:
@@ -197,6 +380,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision / batching / differentiation forms")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()
@@ -220,7 +405,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)     # a real stream: graphs cannot capture the legacy one
+    torch.cuda.set_stream(stream)
 
     w, volt = make_inputs(dev, args.n_time)
     C, Na, N, K, T = len(w["freqs"]), 256, 128, 3, w["n_time"]
@@ -343,6 +529,8 @@ def main():
             "held_gains": held,
             "kernel_sha": sha,
         }
+        if not args.no_forms and world == 1:
+            line["forms"] = forms(torch, Plan, dev, stream, flush, w, volt, args.steps)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w, volt[:, :1].cpu().numpy())
         print(json.dumps(line), flush=True)

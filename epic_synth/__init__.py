@@ -221,6 +221,35 @@ def workload(name: str, seed: int | None = None, n_time: int | None = None,
                     kernel_sigma=0.5, gains=gains, sky=sky, model=pts,
                     n_time=n_time or (10000 if name == "lwa" else 4096),
                     noise_power=noise, input="ci4", gamma=0.5, lsb=lsb, rng=rng)
+    if name == "compact1024":      # Na=1024 in a 200 m disc, 32 ch 40-80 MHz, 256^2, 4-bit
+        rng = np.random.default_rng(2 if seed is None else seed)
+        na = n_ant or 1024
+        ant = layout_disc(na, 200.0, rng, min_sep_m=2.0)
+        nc = n_chan or 32
+        freqs = channels(nc, 40e6, 80e6)
+        gains = true_gains(nc, na, rng)
+        pts = sky_powerlaw(50, 0.5, 50.0, rng)
+        sky = np.vstack([pts, sky_diffuse(1000, pts[:, 2].sum(), rng)])
+        noise = sky[:, 2].sum() / 5.0
+        rms = np.sqrt((sky[:, 2].sum() * np.mean(np.abs(gains) ** 2) + noise) / 2)
+        return dict(ant_xy=ant, freqs=freqs, grid_n=256, cell=0.5, kernel_support=3,
+                    kernel_sigma=0.5, gains=gains, sky=sky, model=pts,
+                    n_time=n_time or 4096, noise_power=noise, input="ci4", gamma=0.5,
+                    lsb=np.full(nc, rms / 2.0), rng=rng)
+    if name == "hex2048":          # Na=2048 hexagonal 8 m pitch +-0.5 m, 256 ch 50-100 MHz, 512^2
+        rng = np.random.default_rng(3 if seed is None else seed)
+        na = n_ant or 2048
+        ant = layout_hex(na, 8.0, 0.5, rng)
+        nc = n_chan or 256
+        freqs = channels(nc, 50e6, 100e6)
+        gains = true_gains(nc, na, rng)
+        pts = sky_powerlaw(50, 0.5, 50.0, rng)
+        sky = np.vstack([pts, sky_diffuse(200, pts[:, 2].sum(), rng)])
+        noise = sky[:, 2].sum() / 5.0
+        return dict(ant_xy=ant, freqs=freqs, grid_n=512, cell=0.5, kernel_support=3,
+                    kernel_sigma=0.5, gains=gains, sky=sky, model=pts,
+                    n_time=n_time or 4096, noise_power=noise, input="c64", gamma=0.5,
+                    lsb=None, rng=rng)
     raise ValueError(name)
 
 
@@ -255,4 +284,46 @@ def voltages_ci4_torch(ant_xy_m, freq_hz, gains, sky_lmS, n_time, noise_power, l
             re = torch.clamp(torch.round(e.real / q), -7, 7).to(torch.int32)
             im = torch.clamp(torch.round(e.imag / q), -7, 7).to(torch.int32)
             out[t0:t0 + n, c, :] = (((re & 15) << 4) | (im & 15)).to(torch.uint8)
+    return out
+
+
+def voltages_c64_torch(ant_xy_m, freq_hz, gains, sky_lmS, n_time, noise_power, seed: int,
+                       device="cuda", chunk: int = 2048):
+    """Large-workload generator: complex64 voltages [T][C][Na] on `device`,
+    same data model as `voltages`, seeded torch.Generator."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    ant = torch.as_tensor(np.asarray(ant_xy_m, np.float64), device=device)
+    sky = torch.as_tensor(np.asarray(sky_lmS, np.float64), device=device)
+    T, C, Na, Ns = int(n_time), len(freq_hz), ant.shape[0], sky.shape[0]
+    out = torch.empty((T, C, Na), dtype=torch.complex64, device=device)
+    amp = torch.sqrt(sky[:, 2]).to(torch.float32)
+    g = torch.as_tensor(np.asarray(gains), device=device).to(torch.complex64)
+    for c, f in enumerate(freq_hz):
+        u = ant * float(f) / C_LIGHT
+        ph = torch.exp(-2j * np.pi * (u @ sky[:, :2].T)).to(torch.complex64)
+        for t0 in range(0, T, chunk):
+            n = min(chunk, T - t0)
+            z = torch.complex(torch.randn((n, Ns), generator=gen, device=device),
+                              torch.randn((n, Ns), generator=gen, device=device)) * (amp / np.sqrt(2.0))
+            e = (z @ ph.T) * g[c][None, :]
+            if noise_power > 0:
+                e = e + torch.complex(torch.randn((n, Na), generator=gen, device=device),
+                                      torch.randn((n, Na), generator=gen, device=device)) * float(
+                                          np.sqrt(noise_power / 2))
+            out[t0:t0 + n, c, :] = e
+    return out
+
+
+def model_frames_c64(ant_xy_m, freq_hz, sky_lmS) -> np.ndarray:
+    """One noise-free frame per model source, sqrt(S_s) exp(-2 pi i u_a . s_s),
+    complex64 [Ns][C][Na]: imaged with unit gains and multiplied by Ns they
+    give the sky-model image sum_s S_s |sum_a A_{k,a} e_a|^2."""
+    ant = np.asarray(ant_xy_m, float)
+    out = np.empty((len(sky_lmS), len(freq_hz), ant.shape[0]), np.complex64)
+    for c, f in enumerate(freq_hz):
+        u = ant * f / C_LIGHT
+        for i, (l, m, S) in enumerate(np.asarray(sky_lmS, float)):
+            out[i, c] = np.sqrt(S) * np.exp(-2j * np.pi * (u[:, 0] * l + u[:, 1] * m))
     return out

@@ -123,7 +123,8 @@ cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStr
 struct TcArgs {
   UnfusedArgs u;           // gridding inputs, grid scratch, image, pixel, EPICal sums
   void* hh;                // [C*N][tb_cap][kp] FP16/BF16 scaled row spectra
-  float* fscale;           // [tb_cap*C] per-frame bound S_f
+  float* fscale;           // [tb_cap*C] per-frame power-of-two scale s_f
+  float* finv2;            // [tb_cap*C] 1 / s_f^2
   int tb_cap, kp, bf16;
   int* err;                // device flag: a bounded wait timed out
 };

@@ -264,7 +264,7 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
     const size_t n_hh = static_cast<size_t>(C) * N * nt * p->kp;
     cudaError_t es[] = {p->d_tc_grid.alloc(n_grid), p->d_tc_hh.alloc(n_hh),
                         p->d_tc_dft.alloc(static_cast<size_t>(2) * N * p->kp),
-                        p->d_tc_scale.alloc(static_cast<size_t>(nt) * C),
+                        p->d_tc_scale.alloc(static_cast<size_t>(2 * nt) * C),
                         p->d_tc_pix.alloc(static_cast<size_t>(nt) * C)};
     for (cudaError_t x : es)
       if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "tensor-path scratch allocation failed");
@@ -321,6 +321,7 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   u.cols_target = p->tune_cols;
   a.hh = p->d_tc_hh.p;
   a.fscale = p->d_tc_scale.p;
+  a.finv2 = p->d_tc_scale.p + static_cast<size_t>(p->tc_time) * C;
   a.tb_cap = p->tc_time;
   a.kp = p->kp;
   a.bf16 = p->precision == EPIC_PREC_BF16 ? 1 : 0;

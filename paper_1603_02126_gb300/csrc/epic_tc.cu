@@ -20,7 +20,8 @@
 // (128B-swizzled, 2-stage ring of data tiles; the CTA's DFT tile is loaded
 // once), warp 1 owns the TMEM allocation and issues tcgen05.mma from one
 // thread (M = 128 DFT rows, N = 128 frames, K = 16 per instruction), warps
-// 2-5 drain the double-buffered TMEM accumulators.  Every mbarrier wait is
+// 2-9 drain the double-buffered TMEM accumulators (two warps per lane
+// quarter, 64 frames each).  Every mbarrier wait is
 // bounded; on timeout the kernel records an error flag and winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -41,12 +42,16 @@ template <> struct LCfg<256> { static constexpr int N1 = 16, N2 = 16; };
 
 constexpr int kLBT = 256;
 
-// Largest power of two s with s * S < 1 (S > 0), from the float's exponent.
-__device__ __forceinline__ float pow2_below_inverse(float S) {
-  if (!(S > 0.f)) return 1.0f;
+// Exponent k of the largest power of two s = 2^k with s * S < 1 (S > 0),
+// from the float's exponent field, clamped to [-60, 60] so that s and 1/s^2
+// are normal floats.
+__device__ __forceinline__ int pow2_exp_below_inverse(float S) {
+  if (!(S > 0.f)) return 0;
   const int e = static_cast<int>((__float_as_uint(S) >> 23) & 0xff) - 127;
   int k = -(e + 1);
-  k = k < -126 ? -126 : (k > 127 ? 127 : k);
+  return k < -60 ? -60 : (k > 60 ? 60 : k);
+}
+__device__ __forceinline__ float exp2i(int k) {   // 2^k for k in [-126, 127]
   return __uint_as_float(static_cast<unsigned>(k + 127) << 23);
 }
 
@@ -60,10 +65,12 @@ __device__ __forceinline__ float2 load_volt_tc(const void* volt, int fmt, size_t
   return __ldg(static_cast<const float2*>(volt) + idx);
 }
 
-template <typename T> __device__ __forceinline__ T to_lp(float x);
-template <> __device__ __forceinline__ __half to_lp<__half>(float x) { return __float2half_rn(x); }
-template <> __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
+// (re, im) rounded to the storage type, as one 4-byte store.
+__device__ __forceinline__ void store_lp(__half* dst, float re, float im) {
+  *reinterpret_cast<__half2*>(dst) = __floats2half2_rn(re, im);
+}
+__device__ __forceinline__ void store_lp(__nv_bfloat16* dst, float re, float im) {
+  *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(re, im);
 }
 
 // ---- S_f: one warp per frame ----
@@ -84,7 +91,11 @@ __global__ void frame_scale_kernel(const TcArgs A, long long t0, int nt) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(fft::kFull, s, o);
-  if (lane == 0) A.fscale[warp] = s / static_cast<float>(Na);
+  if (lane == 0) {
+    const int k = pow2_exp_below_inverse(s / static_cast<float>(Na));
+    A.fscale[warp] = exp2i(k);        // s_f: multiplies the row spectra
+    A.finv2[warp] = exp2i(-2 * k);    // 1 / s_f^2: multiplies |D|^2
+  }
 }
 
 // ---- FP32 row FFTs, low-precision K-major output, FP32 calibrator pixel ----
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, int nt) {
 #pragma unroll
     for (int j = 0; j < N2; ++j) v[j] = src[n1 + N1 * j];
     fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
-    const float s = pow2_below_inverse(__ldg(A.fscale + f));
+    const float s = __ldg(A.fscale + f);
 #pragma unroll
     for (int h = 0; h < H; ++h)
 #pragma unroll
@@ -128,8 +139,7 @@ __global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, int nt) {
         const int kx = n1 + N1 * h + N2 * k1;
         const float2 x = v[h * N1 + k1];
         T* dst = hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * row;
-        dst[0] = to_lp<T>(x.x * s);
-        dst[1] = to_lp<T>(x.y * s);
+        store_lp(dst, x.x * s, x.y * s);
       }
     if (A.u.do_cal && n1 == pn1) {
       // pixel (k0x, k0y): sum over rows of X[jy][k0x] e^{+2 pi i jy k0y / N}
@@ -251,7 +261,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int kTcThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTcThreads = 320;          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiWarps = 8;             // two per TMEM lane quarter, each half the frames
 constexpr int kTile = 128;               // DFT rows and frames per tile
 constexpr int kChunkBytes = kTile * 128; // one 64-element K chunk of a 128-row tile
 constexpr uint32_t kTmemCols = 256;      // two 128-column accumulators
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(smem_u32(bars + i), 1);
       mbar_init(smem_u32(bars + 2 + i), 1);
       mbar_init(smem_u32(bars + 4 + i), 1);
-      mbar_init(smem_u32(bars + 6 + i), 4);
+      mbar_init(smem_u32(bars + 6 + i), kEpiWarps);
     }
     mbar_init(smem_u32(bars + 8), 1);
     *abort_flag = 0;
@@ -360,8 +371,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2-5) ----------------
+    // ---------------- epilogue (warps 2-9) ----------------
     const int q = warp & 3;                        // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;              // which 64 frames of the tile
     const int r = mb * kTile + q * 32 + lane;      // DFT row = 2 ky + (re, im)
     const int ky = r >> 1;
     int i = 0;
@@ -375,21 +387,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const long long ck = rest / tbk;
       const int c = static_cast<int>(ck / N), kx = static_cast<int>(ck % N);
       float sum = 0.f;
-#pragma unroll 1
-      for (int ch = 0; ch < kTile / 32; ++ch) {
+#pragma unroll
+      for (int ch = 0; ch < kTile / 64; ++ch) {
+        const int col = half * 64 + ch * 32;
+        const int t = tb * kTile + col + lane;
+        const float my_w = (t < nt) ? __ldg(A.finv2 + static_cast<size_t>(t) * C + c) : 0.f;
         float v[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32),
-                  v);
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + col), v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int t = tb * kTile + ch * 32 + j;
-          float w = 0.f;
-          if (t < nt) {
-            const float s = pow2_below_inverse(__ldg(A.fscale + static_cast<size_t>(t) * C + c));
-            const float inv = 1.0f / s;            // exact: s is a power of two
-            w = inv * inv;
-          }
-          sum += v[j] * v[j] * w;
+          const float w = __shfl_sync(fft::kFull, my_w, j);
+          sum = fmaf(v[j] * v[j], w, sum);
         }
       }
       tc_fence_before();
