@@ -78,6 +78,36 @@ struct Dft<1> {
 };
 
 
+// R-point DFT of an input whose entries x[j], j >= NZ, are zero: the
+// butterflies and copies that would only involve those zeros are skipped
+// (compile-time pruning of the decimation-in-time recursion).
+template <int R, int NZ>
+struct DftP {
+  static __device__ __forceinline__ void run(float2 (&x)[R]) {
+    if constexpr (NZ >= R) {
+      Dft<R>::run(x);
+    } else if constexpr (NZ <= 1) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) x[k] = x[0];
+    } else {
+      float2 e[R / 2], o[R / 2];
+#pragma unroll
+      for (int i = 0; i < R / 2; ++i) {
+        e[i] = x[2 * i];
+        o[i] = x[2 * i + 1];
+      }
+      DftP<R / 2, (NZ + 1) / 2>::run(e);
+      DftP<R / 2, NZ / 2>::run(o);
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        const float2 t = twiddle<R>(o[k], k);
+        x[k] = cadd(e[k], t);
+        x[k + R / 2] = csub(e[k], t);
+      }
+    }
+  }
+};
+
 // Padded exchange geometry of fft_lanes<N1, N2>.
 template <int N1, int N2>
 struct Xchg {
@@ -98,6 +128,30 @@ __device__ __forceinline__ void fft_lanes(float2 (&v)[N2], int n1, float2* z, co
                                           unsigned gmask) {
   constexpr int ZS = Xchg<N1, N2>::ZS, H = Xchg<N1, N2>::H;
   Dft<N2>::run(v);
+#pragma unroll
+  for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) z[k2 * ZS + n1] = v[k2];
+  __syncwarp(gmask);
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    float2 u[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) u[m] = z[(n1 + N1 * h) * ZS + m];
+    Dft<N1>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[h * N1 + k1] = u[k1];
+  }
+  __syncwarp(gmask);
+}
+
+// fft_lanes for inputs that are zero beyond index N1 * NZ: v[j] for j >= NZ
+// must be zero on entry (they are not read by the first-stage DFT).
+template <int N1, int N2, int NZ>
+__device__ __forceinline__ void fft_lanes_p(float2 (&v)[N2], int n1, float2* z, const float2* tw,
+                                            unsigned gmask) {
+  constexpr int ZS = Xchg<N1, N2>::ZS, H = Xchg<N1, N2>::H;
+  DftP<N2, NZ>::run(v);
 #pragma unroll
   for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
 #pragma unroll

@@ -20,6 +20,9 @@ struct ImageArgs {
   const float2* wgain;     // [C][Na] 1/g (gain correction multiplier)
   const float* vscale;     // [C] voltage scale, or nullptr
   const int2* win;         // [C] (first occupied grid row y0, occupied rows R)
+  const int4* win4;        // [C] (y0, rows, x0, columns) of the occupied window
+  const int* cellf;        // [C][Na] window cell (row * (N + N1) + col - x0); -1 = flagged
+  const float2* pixph;     // [C] (-1)^(k0x+k0y) e^{2 pi i (x0 k0x + y0 k0y)/N}
   const float2* twid;      // [N] e^{+2 pi i m / N}
   double* image;           // [C][N][N] accumulated with img_scale
   double img_scale;        // 1 / T_call
@@ -30,7 +33,7 @@ struct ImageArgs {
   double* pacc;            // [C][Na] sum_t |E_a|^2
   int segs;                // time segments per channel (units = C * segs)
   int rows_alloc;          // shared-memory grid rows (max R)
-  int rs;                  // row stride of the transposed buffer
+  int rs;                  // row stride of the transposed (swizzled) buffer
   int grid;                // CTAs launched
   size_t smem;             // dynamic shared memory bytes
 };
@@ -44,6 +47,12 @@ struct ImageKernelShape {
 
 bool image_kernel_shape(int n, ImageKernelShape* out);
 int image_rs(int rows_alloc);
+int image_rs_fused(int rows_alloc);
+// Dynamic shared memory of the adjoint kernel (layout: window [rows][N],
+// spectra [N][rs], FFT exchange, twiddles).
+size_t adjoint_smem_bytes(int n, int rows_alloc, int rs);
+// Row stride of the fused kernel's grid window, N + N1.
+int image_window_stride(int n);
 size_t image_smem_bytes(int n, int rows_alloc, int rs);
 // Opt in to the shared memory and report resident CTAs per SM.
 cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas_per_sm);

@@ -90,217 +90,242 @@ __device__ __forceinline__ float2 load_volt(const ImageArgs& A, long long t, int
   return __ldg(static_cast<const float2*>(A.volt) + idx);
 }
 
-template <int N, int MAXA>
-__global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
+// One work unit (channel c, frames [t0, t1)) of the fused kernel, for an
+// occupied window of at most N1 * NZ rows and columns: the grid is kept in
+// window coordinates (first occupied row and column at 0), which only
+// changes the phase of each image pixel, so every 1-D FFT has at most NZ
+// non-zero inputs per lane and uses the pruned first-stage DFT.
+template <int N, int MAXA, int NZ>
+__device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long t0, long long t1,
+                                           float2* Wg, float2* Tt, float2* zg, const float2* tw,
+                                           float2* pixs) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][N] grid window
-  float2* Tt = Wg + A.rows_alloc * N;                  // [N][rs] row spectra, transposed
-  float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
-  float2* tw = Z + GROUPS * G::ZG;                     // [N] twiddles
-  float2* pixs = tw + N;                               // calibrator pixel
-
+  constexpr int WS = N + N1;                           // grid-window row stride
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int g = tid / N1;
   const int n1 = tid % N1;
-  const unsigned gmask = (N1 == 32) ? kFull : (((1u << N1) - 1u) << (lane & ~(N1 - 1)));
-  float2* zg = Z + g * G::ZG;
-
-  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
-  for (int i = tid; i < A.rows_alloc * N; i += BT) Wg[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-
+  const unsigned gmask = fft::group_mask<N1>(lane);
   const int Na = A.n_ant;
   const int K = A.support;
   const int KK = K * K;
   const int items = K * Na;
   const int items_pad = ((items + BT - 1) / BT) * BT;
-  const long long T = A.n_time;
-  const int units = A.n_chan * A.segs;
+  const int rs = A.rs;
 
-  // calibrator pixel: column round, group, lane and register slot
+  const int4 wn = __ldg(A.win4 + c);                   // (y0, rows, x0, cols)
+  const int R = wn.y;
+  const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+  const int* cellf = A.cellf + static_cast<size_t>(c) * Na;
+  const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
+  const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
+
+  // calibrator pixel: column round, group, lane and register slot, phase
   const int pr = A.k0x / GROUPS, pg = A.k0x % GROUPS;
   const int pn1 = A.k0y % N1;
   const int pq = A.k0y / N1;
   const int pslot = (pq % H) * N1 + pq / H;
   const bool pix_owner = A.do_cal && g == pg && n1 == pn1;
+  const float2 pph = A.do_cal ? __ldg(A.pixph + c) : make_float2(1.f, 0.f);
 
+  float acc[G::NACC];
+#pragma unroll
+  for (int i = 0; i < G::NACC; ++i) acc[i] = 0.f;
+  float2 kac[MAXA], ecur[MAXA];
+  float pac[MAXA];
+#pragma unroll
+  for (int i = 0; i < MAXA; ++i) {
+    kac[i] = make_float2(0.f, 0.f);
+    ecur[i] = make_float2(0.f, 0.f);
+    pac[i] = 0.f;
+  }
+
+  for (long long t = t0; t < t1; ++t) {
+    // ---- A: raw voltages for the correlation, then gain + scatter ----
+    float2 eprev[MAXA];
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      eprev[i] = ecur[i];
+      const int a = tid + BT * i;
+      if (A.do_cal && a < Na) {
+        const float2 e = load_volt(A, t, c, a);
+        ecur[i] = make_float2(e.x * vs, e.y * vs);
+      }
+    }
+    for (int it = tid; it < items_pad; it += BT) {
+      const bool in = it < items;
+      const int a = in ? it % Na : 0;
+      const int dy = in ? it / Na : 0;
+      const int c0 = in ? __ldg(cellf + a) : -1;
+      const bool valid = c0 >= 0;
+      float2 ec = make_float2(0.f, 0.f);
+      if (valid) {
+        const float2 e = load_volt(A, t, c, a);
+        ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
+      }
+      const int rowcell = valid ? c0 + dy * WS : -1 - lane;
+      const unsigned peers = __match_any_sync(kFull, rowcell);
+      const bool dup = __popc(peers) > 1;
+      const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
+      if (!__any_sync(kFull, dup)) {
+        if (valid) {
+          for (int dx = 0; dx < K; ++dx) {
+            const float w = __ldg(wrow + dx);
+            atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
+            atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
+          }
+        }
+      } else {
+        // lanes sharing a cell: the lowest lane adds the group's sum
+        const int leader = __ffs(peers) - 1;
+        for (int dx = 0; dx < K; ++dx) {
+          const float w = valid ? __ldg(wrow + dx) : 0.f;
+          const float vx = w * ec.x, vy = w * ec.y;
+          float sx = 0.f, sy = 0.f;
+#pragma unroll
+          for (int src = 0; src < 32; ++src) {
+            const float ox = __shfl_sync(kFull, vx, src);
+            const float oy = __shfl_sync(kFull, vy, src);
+            if ((peers >> src) & 1u) {
+              sx += ox;
+              sy += oy;
+            }
+          }
+          if (valid && lane == leader) {
+            atomicAdd(&Wg[rowcell + dx].x, sx);
+            atomicAdd(&Wg[rowcell + dx].y, sy);
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- B: correlation of the previous frame, then row FFTs ----
+    if (A.do_cal && t > t0) {
+      const float2 p = pixs[0];
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const float2 e = eprev[i];
+        kac[i].x += e.x * p.x + e.y * p.y;
+        kac[i].y += e.y * p.x - e.x * p.y;
+        pac[i] += e.x * e.x + e.y * e.y;
+      }
+    }
+    for (int row = g; row < R; row += GROUPS) {
+      float2 v[N2];
+      float2* wr = Wg + row * WS;
+#pragma unroll
+      for (int j = 0; j < N2; ++j) v[j] = (j < NZ) ? wr[n1 + N1 * j] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NZ; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const int kx = n1 + N1 * h + N2 * k1;
+          Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
+        }
+    }
+    __syncthreads();
+
+    // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
+#pragma unroll
+    for (int r = 0; r < G::COLROUNDS; ++r) {
+      const int kx = g + GROUPS * r;
+      float2 v[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) {
+        const int jw = n1 + N1 * j;
+        v[j] = (j < NZ && jw < R) ? Tt[kx * rs + (jw ^ (kx & 7))] : make_float2(0.f, 0.f);
+      }
+      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
+#pragma unroll
+      for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
+      if (pix_owner && r == pr) {
+#pragma unroll
+        for (int q = 0; q < N2; ++q)
+          if (q == pslot) pixs[0] = cmul(v[q], pph);
+      }
+    }
+  }
+  __syncthreads();
+
+  // correlation of the unit's last frame
+  if (A.do_cal) {
+    const float2 p = pixs[0];
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const float2 e = ecur[i];
+      kac[i].x += e.x * p.x + e.y * p.y;
+      kac[i].y += e.y * p.x - e.x * p.y;
+      pac[i] += e.x * e.x + e.y * e.y;
+    }
+  }
+
+  // flush the unit's partial sums (FP32 over one segment, FP64 across)
+  double* img = A.image + static_cast<size_t>(c) * N * N;
+#pragma unroll
+  for (int r = 0; r < G::COLROUNDS; ++r) {
+    const int kx = g + GROUPS * r;
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int ky = n1 + N1 * h + N2 * k1;
+        atomicAdd(img + ky * N + kx, static_cast<double>(acc[r * N2 + h * N1 + k1]) * A.img_scale);
+      }
+  }
+  if (A.do_cal) {
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
+      if (a < Na && cellf[a] >= 0) {
+        const size_t o = static_cast<size_t>(c) * Na + a;
+        atomicAdd(&A.kacc[o].x, static_cast<double>(kac[i].x));
+        atomicAdd(&A.kacc[o].y, static_cast<double>(kac[i].y));
+        atomicAdd(A.pacc + o, static_cast<double>(pac[i]));
+      }
+    }
+  }
+}
+
+template <int N, int MAXA>
+__global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
+  using G = Geo<N>;
+  constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS;
+  constexpr int WS = N + N1;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][WS] grid window
+  float2* Tt = Wg + A.rows_alloc * WS;                 // [N][rs] row spectra, transposed, swizzled
+  float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
+  float2* tw = Z + GROUPS * G::ZG;                     // [N] twiddles
+  float2* pixs = tw + N;                               // calibrator pixel
+
+  const int tid = threadIdx.x;
+  float2* zg = Z + (tid / N1) * G::ZG;
+  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
+  for (int i = tid; i < A.rows_alloc * WS; i += BT) Wg[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const long long T = A.n_time;
+  const int units = A.n_chan * A.segs;
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
     const int c = u / A.segs;
     const int s = u - c * A.segs;
     const long long t0 = T * s / A.segs;
     const long long t1 = T * (s + 1) / A.segs;
     if (t0 >= t1) continue;
-    const int2 wn = __ldg(A.win + c);
-    const int y0 = wn.x, R = wn.y;
-    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
-    const int* cell0 = A.cell0 + static_cast<size_t>(c) * Na;
-    const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
-    const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
-
-    float acc[G::NACC];
-#pragma unroll
-    for (int i = 0; i < G::NACC; ++i) acc[i] = 0.f;
-    float2 kac[MAXA], ecur[MAXA];
-    float pac[MAXA];
-#pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      kac[i] = make_float2(0.f, 0.f);
-      ecur[i] = make_float2(0.f, 0.f);
-      pac[i] = 0.f;
-    }
-
-    for (long long t = t0; t < t1; ++t) {
-      // ---- A: raw voltages for the correlation, then gain + scatter ----
-      float2 eprev[MAXA];
-#pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        eprev[i] = ecur[i];
-        const int a = tid + BT * i;
-        if (A.do_cal && a < Na) {
-          const float2 e = load_volt(A, t, c, a);
-          ecur[i] = make_float2(e.x * vs, e.y * vs);
-        }
-      }
-      for (int it = tid; it < items_pad; it += BT) {
-        const bool in = it < items;
-        const int a = in ? it % Na : 0;
-        const int dy = in ? it / Na : 0;
-        const int c0 = in ? __ldg(cell0 + a) : -1;
-        const bool valid = c0 >= 0;
-        float2 ec = make_float2(0.f, 0.f);
-        if (valid) {
-          const float2 e = load_volt(A, t, c, a);
-          ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
-        }
-        const int rowcell = valid ? c0 + dy * N : -1 - lane;
-        const unsigned peers = __match_any_sync(kFull, rowcell);
-        const bool dup = __popc(peers) > 1;
-        const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
-        if (!__any_sync(kFull, dup)) {
-          if (valid) {
-            for (int dx = 0; dx < K; ++dx) {
-              const float w = __ldg(wrow + dx);
-              atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
-              atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
-            }
-          }
-        } else {
-          // lanes sharing a cell: the lowest lane adds the group's sum
-          const int leader = __ffs(peers) - 1;
-          for (int dx = 0; dx < K; ++dx) {
-            const float w = valid ? __ldg(wrow + dx) : 0.f;
-            const float vx = w * ec.x, vy = w * ec.y;
-            float sx = 0.f, sy = 0.f;
-#pragma unroll
-            for (int src = 0; src < 32; ++src) {
-              const float ox = __shfl_sync(kFull, vx, src);
-              const float oy = __shfl_sync(kFull, vy, src);
-              if ((peers >> src) & 1u) {
-                sx += ox;
-                sy += oy;
-              }
-            }
-            if (valid && lane == leader) {
-              atomicAdd(&Wg[rowcell + dx].x, sx);
-              atomicAdd(&Wg[rowcell + dx].y, sy);
-            }
-          }
-        }
-      }
-      __syncthreads();
-
-      // ---- B: correlation of the previous frame, then row FFTs ----
-      if (A.do_cal && t > t0) {
-        const float2 p = pixs[0];
-#pragma unroll
-        for (int i = 0; i < MAXA; ++i) {
-          const float2 e = eprev[i];
-          kac[i].x += e.x * p.x + e.y * p.y;
-          kac[i].y += e.y * p.x - e.x * p.y;
-          pac[i] += e.x * e.x + e.y * e.y;
-        }
-      }
-      for (int row = g; row < R; row += GROUPS) {
-        float2 v[N2];
-        float2* wr = Wg + row * N;
-#pragma unroll
-        for (int j = 0; j < N2; ++j) v[j] = wr[n1 + N1 * j];
-#pragma unroll
-        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
-        fft_group<N>(v, n1, zg, tw, gmask);
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const int kx = n1 + N1 * h + N2 * k1;
-            Tt[kx * A.rs + row] = v[h * N1 + k1];
-          }
-      }
-      __syncthreads();
-
-      // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
-#pragma unroll
-      for (int r = 0; r < G::COLROUNDS; ++r) {
-        const int kx = g + GROUPS * r;
-        float2 v[N2];
-#pragma unroll
-        for (int j = 0; j < N2; ++j) {
-          const int jw = n1 + N1 * j - y0;
-          v[j] = (jw >= 0 && jw < R) ? Tt[kx * A.rs + jw] : make_float2(0.f, 0.f);
-        }
-        fft_group<N>(v, n1, zg, tw, gmask);
-#pragma unroll
-        for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
-        if (pix_owner && r == pr) {
-#pragma unroll
-          for (int q = 0; q < N2; ++q)
-            if (q == pslot) pixs[0] = make_float2(v[q].x * A.pix_sign, v[q].y * A.pix_sign);
-        }
-      }
-    }
-    __syncthreads();
-
-    // correlation of the unit's last frame
-    if (A.do_cal) {
-      const float2 p = pixs[0];
-#pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        const float2 e = ecur[i];
-        kac[i].x += e.x * p.x + e.y * p.y;
-        kac[i].y += e.y * p.x - e.x * p.y;
-        pac[i] += e.x * e.x + e.y * e.y;
-      }
-    }
-
-    // flush the unit's partial sums (FP32 over one segment, FP64 across)
-    double* img = A.image + static_cast<size_t>(c) * N * N;
-#pragma unroll
-    for (int r = 0; r < G::COLROUNDS; ++r) {
-      const int kx = g + GROUPS * r;
-#pragma unroll
-      for (int h = 0; h < H; ++h)
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const int ky = n1 + N1 * h + N2 * k1;
-          atomicAdd(img + ky * N + kx, static_cast<double>(acc[r * N2 + h * N1 + k1]) * A.img_scale);
-        }
-    }
-    if (A.do_cal) {
-#pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        const int a = tid + BT * i;
-        if (a < Na && cell0[a] >= 0) {
-          const size_t o = static_cast<size_t>(c) * Na + a;
-          atomicAdd(&A.kacc[o].x, static_cast<double>(kac[i].x));
-          atomicAdd(&A.kacc[o].y, static_cast<double>(kac[i].y));
-          atomicAdd(A.pacc + o, static_cast<double>(pac[i]));
-        }
-      }
-    }
+    const int4 wn = __ldg(A.win4 + c);
+    const int span = wn.y > wn.w ? wn.y : wn.w;          // occupied rows / columns
+    if (span <= N1 * (N2 / 4))
+      fused_unit<N, MAXA, N2 / 4>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
+    else if (span <= N1 * (N2 / 2))
+      fused_unit<N, MAXA, N2 / 2>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
+    else
+      fused_unit<N, MAXA, N2>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
   }
 }
 
@@ -674,6 +699,16 @@ cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, 
   return cudaGetLastError();
 }
 
+int image_window_stride(int n) {
+  switch (n) {
+    case 16: return 16 + Geo<16>::N1;
+    case 32: return 32 + Geo<32>::N1;
+    case 64: return 64 + Geo<64>::N1;
+    case 128: return 128 + Geo<128>::N1;
+    default: return 0;
+  }
+}
+
 bool image_kernel_shape(int n, ImageKernelShape* out) {
   switch (n) {
     case 16: shape_n<16>(out); return true;
@@ -690,7 +725,7 @@ int image_rs(int rows_alloc) {
   return rs;
 }
 
-size_t image_smem_bytes(int n, int rows_alloc, int rs) {
+size_t adjoint_smem_bytes(int n, int rows_alloc, int rs) {
   int groups = 0, zg = 0;
   switch (n) {
     case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
@@ -699,7 +734,28 @@ size_t image_smem_bytes(int n, int rows_alloc, int rs) {
     case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
     default: return 0;
   }
+  // grid window [rows][N], transposed / row-major spectra [N][rs], exchange, twiddles
   const size_t elems = static_cast<size_t>(rows_alloc) * n + static_cast<size_t>(n) * rs +
+                       static_cast<size_t>(groups) * zg + n;
+  return elems * sizeof(float2);
+}
+
+int image_rs_fused(int rows_alloc) {
+  int rs = ((rows_alloc + 7) / 8) * 8;     // room for the (row ^ (kx & 7)) swizzle
+  while (rs % 16 != 8) rs += 8;
+  return rs;
+}
+
+size_t image_smem_bytes(int n, int rows_alloc, int rs) {
+  int groups = 0, zg = 0, n1 = 0;
+  switch (n) {
+    case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; n1 = Geo<16>::N1; break;
+    case 32: groups = Geo<32>::GROUPS; zg = Geo<32>::ZG; n1 = Geo<32>::N1; break;
+    case 64: groups = Geo<64>::GROUPS; zg = Geo<64>::ZG; n1 = Geo<64>::N1; break;
+    case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; n1 = Geo<128>::N1; break;
+    default: return 0;
+  }
+  const size_t elems = static_cast<size_t>(rows_alloc) * (n + n1) + static_cast<size_t>(n) * rs +
                        static_cast<size_t>(groups) * zg + n + 2;
   return elems * sizeof(float2);
 }

@@ -86,6 +86,11 @@ struct epic_plan_s {
   DevBuf<double2> d_gain;       // [C][Na] g
   DevBuf<float> d_vscale;       // [C]
   DevBuf<int2> d_win;           // [C]
+  DevBuf<int4> d_win4;          // [C] (y0, rows, x0, cols) for the fused kernel
+  DevBuf<int> d_cellf;          // [C][Na] fused-kernel window cell of tap (0,0)
+  DevBuf<float2> d_pixph;       // [C] calibrator-pixel phase in window coordinates
+  std::vector<int> x0, cols;    // [C] first occupied column, occupied columns
+  int rs_fused = 0;
   DevBuf<float2> d_twid;        // [N]
   DevBuf<unsigned char> d_flags;  // [Na]
 
@@ -160,6 +165,42 @@ int choose_segments(int n_chan, long long n_time, int ctas, int target = 4) {
     if (units >= 4LL * target * ctas) return static_cast<int>(s);
   }
   return static_cast<int>(best);
+}
+
+// Arguments of one fused launch over a device batch.
+epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
+                           double img_scale) {
+  epic::ImageArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.cell0 = p->d_cell0.p;
+  a.cellf = p->d_cellf.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win = p->d_win.p;
+  a.win4 = p->d_win4.p;
+  a.pixph = p->d_pixph.p;
+  a.twid = p->d_twid.p;
+  a.image = d_image;
+  a.img_scale = img_scale;
+  a.do_cal = p->cal ? 1 : 0;
+  a.k0x = p->cal ? p->k0x : 0;
+  a.k0y = p->cal ? p->k0y : 0;
+  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
+  a.kacc = p->d_kacc.p;
+  a.pacc = p->d_pacc.p;
+  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
+  a.rows_alloc = p->rows_alloc;
+  a.rs = p->rs_fused;
+  const long long units = static_cast<long long>(p->nc) * a.segs;
+  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
+  a.smem = p->smem;
+  return a;
 }
 
 // Plain unfused path: batches of time samples through the device scratch.
@@ -407,6 +448,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   p->w64.assign(static_cast<size_t>(C) * Na * KK, 0.0);
   p->y0.assign(C, 0);
   p->rows.assign(C, 0);
+  p->x0.assign(C, 0);
+  p->cols.assign(C, 0);
   std::vector<int> cell0(static_cast<size_t>(C) * Na, -1);
   std::vector<float> wts(static_cast<size_t>(C) * Na * KK, 0.0f);
   int n_unflagged = 0;
@@ -467,6 +510,15 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
     p->y0[c] = ymin;
     p->rows[c] = ymax - ymin + 1;
+    int xmin = N, xmax = -1;
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const int bx = p->base[(static_cast<size_t>(c) * Na + a) * 2];
+      xmin = std::min(xmin, bx - h);
+      xmax = std::max(xmax, bx + h);
+    }
+    p->x0[c] = xmin;
+    p->cols[c] = xmax - xmin + 1;
     p->rows_alloc = std::max(p->rows_alloc, p->rows[c]);
     for (int a = 0; a < Na; ++a) {
       if (p->flags[a]) continue;
@@ -511,8 +563,9 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       return cuda_fail(e, "tensor-core kernel attributes");
     }
   }
+  p->rs_fused = epic::image_rs_fused(p->rows_alloc);
   if (fused) {
-    p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs);
+    p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs_fused);
     if (p->smem > static_cast<size_t>(smem_optin)) {
       const std::string msg = "array footprint needs " + std::to_string(p->smem) +
                               " B of shared memory in the fused kernel (limit " +
@@ -547,6 +600,18 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                           static_cast<float>(std::sin(2.0 * kPi * m / N)));
   std::vector<int2> win(C);
   for (int c = 0; c < C; ++c) win[c] = make_int2(p->y0[c], p->rows[c]);
+  std::vector<int4> win4(C);
+  for (int c = 0; c < C; ++c) win4[c] = make_int4(p->y0[c], p->rows[c], p->x0[c], p->cols[c]);
+  std::vector<int> cellf(static_cast<size_t>(C) * Na, -1);
+  const int ws = fused ? epic::image_window_stride(N) : N;
+  for (int c = 0; c < C; ++c)
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      const int bx = p->base[ob], by = p->base[ob + 1];
+      cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
+    }
+  std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
   std::vector<double2> gain(static_cast<size_t>(C) * Na, make_double2(1.0, 0.0));
   std::vector<float2> wgain(static_cast<size_t>(C) * Na, make_float2(1.0f, 0.0f));
 
@@ -557,7 +622,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   };
   cudaError_t es[] = {up(p->d_cell0, cell0), up(p->d_wts, wts), up(p->d_wgain, wgain),
                       up(p->d_gain, gain), up(p->d_vscale, p->vscale), up(p->d_win, win),
-                      up(p->d_twid, twid), up(p->d_flags, p->flags)};
+                      up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
+                      up(p->d_cellf, cellf), up(p->d_pixph, pixph)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -585,6 +651,9 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_gain.release();
   p->d_vscale.release();
   p->d_win.release();
+  p->d_win4.release();
+  p->d_cellf.release();
+  p->d_pixph.release();
   p->d_twid.release();
   p->d_flags.release();
   p->d_a0.release();
@@ -663,33 +732,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_image, 0, img_bytes, p->stream));
   if (p->precision != EPIC_PREC_FP32) return image_tc(p, d_volt, n_time, d_image);
   if (p->path == EPIC_PATH_UNFUSED) return image_unfused(p, d_volt, n_time, d_image);
-  epic::ImageArgs a{};
-  a.volt = d_volt;
-  a.input_fmt = p->input;
-  a.n_time = n_time;
-  a.n_chan = p->nc;
-  a.n_ant = p->na;
-  a.support = p->k;
-  a.cell0 = p->d_cell0.p;
-  a.wts = p->d_wts.p;
-  a.wgain = p->d_wgain.p;
-  a.vscale = p->d_vscale.p;
-  a.win = p->d_win.p;
-  a.twid = p->d_twid.p;
-  a.image = d_image;
-  a.img_scale = 1.0 / static_cast<double>(n_time);
-  a.do_cal = p->cal ? 1 : 0;
-  a.k0x = p->cal ? p->k0x : 0;
-  a.k0y = p->cal ? p->k0y : 0;
-  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
-  a.kacc = p->d_kacc.p;
-  a.pacc = p->d_pacc.p;
-  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
-  a.rows_alloc = p->rows_alloc;
-  a.rs = p->rs;
-  const long long units = static_cast<long long>(p->nc) * a.segs;
-  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
-  a.smem = p->smem;
+  const epic::ImageArgs a = fused_args(p, d_volt, n_time, d_image, 1.0 / static_cast<double>(n_time));
   EPIC_CUDA(epic::launch_image(p->n, a, p->stream));
   if (p->cal) p->frames += n_time;
   return EPIC_OK;
@@ -800,6 +843,20 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   EPIC_CUDA(cudaMemcpyAsync(p->d_dden.p, dd.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+  {
+    // pixel k0 of the window-coordinate transform: sign * e^{2 pi i (x0 k0x + y0 k0y) / N}
+    std::vector<float2> ph(C);
+    const double sg = ((k0x + k0y) & 1) ? -1.0 : 1.0;
+    for (int c = 0; c < C; ++c) {
+      long long m = static_cast<long long>(p->x0[c]) * k0x + static_cast<long long>(p->y0[c]) * k0y;
+      m %= N;
+      if (m < 0) m += N;
+      const double th = 2.0 * kPi * static_cast<double>(m) / N;
+      ph[c] = make_float2(static_cast<float>(sg * std::cos(th)), static_cast<float>(sg * std::sin(th)));
+    }
+    EPIC_CUDA(cudaMemcpyAsync(p->d_pixph.p, ph.data(), C * sizeof(float2), cudaMemcpyHostToDevice,
+                              p->stream));
+  }
   EPIC_CUDA(cudaMemsetAsync(p->d_kacc.p, 0, n * sizeof(double2), p->stream));
   EPIC_CUDA(cudaMemsetAsync(p->d_pacc.p, 0, n * sizeof(double), p->stream));
   EPIC_CUDA(cudaStreamSynchronize(p->stream));
@@ -1134,7 +1191,7 @@ epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_t
   a.rs = p->rs;
   const long long units = static_cast<long long>(p->nc) * a.segs;
   a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
-  a.smem = p->smem;
+  a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs);
   EPIC_CUDA(epic::launch_adjoint(p->n, a, p->stream));
   EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_flags.p,
                                           reinterpret_cast<double2*>(d_grad_g), p->stream));
@@ -1165,33 +1222,7 @@ int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, dou
   if (!p || !d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad batch");
   if (p->path != EPIC_PATH_FUSED)
     return fail(EPIC_ERR_UNSUPPORTED, "this call needs a plan on the fused path");
-  ImageArgs a{};
-  a.volt = d_volt;
-  a.input_fmt = p->input;
-  a.n_time = n_time;
-  a.n_chan = p->nc;
-  a.n_ant = p->na;
-  a.support = p->k;
-  a.cell0 = p->d_cell0.p;
-  a.wts = p->d_wts.p;
-  a.wgain = p->d_wgain.p;
-  a.vscale = p->d_vscale.p;
-  a.win = p->d_win.p;
-  a.twid = p->d_twid.p;
-  a.image = d_image;
-  a.img_scale = img_scale;
-  a.do_cal = p->cal ? 1 : 0;
-  a.k0x = p->cal ? p->k0x : 0;
-  a.k0y = p->cal ? p->k0y : 0;
-  a.pix_sign = ((a.k0x + a.k0y) & 1) ? -1.0f : 1.0f;
-  a.kacc = p->d_kacc.p;
-  a.pacc = p->d_pacc.p;
-  a.segs = choose_segments(p->nc, n_time, p->ctas, p->tune_units);
-  a.rows_alloc = p->rows_alloc;
-  a.rs = p->rs;
-  const long long units = static_cast<long long>(p->nc) * a.segs;
-  a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
-  a.smem = p->smem;
+  const ImageArgs a = fused_args(p, d_volt, n_time, d_image, img_scale);
   cudaError_t e = launch_image(p->n, a, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "image launch");
   if (p->cal) p->frames += n_time;
