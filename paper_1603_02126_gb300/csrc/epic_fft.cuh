@@ -146,14 +146,16 @@ __device__ __forceinline__ void fft_lanes(float2 (&v)[N2], int n1, float2* z, co
 }
 
 // fft_lanes for inputs that are zero beyond index N1 * NZ: v[j] for j >= NZ
-// must be zero on entry (they are not read by the first-stage DFT).
+// must be zero on entry (they are not read by the first-stage DFT).  tw2 is
+// the twiddle table ordered [k2][n1] (tw2[k2 * N1 + n1] = e^{+2 pi i n1 k2 / N}),
+// so that the lanes of a group read consecutive entries.
 template <int N1, int N2, int NZ>
-__device__ __forceinline__ void fft_lanes_p(float2 (&v)[N2], int n1, float2* z, const float2* tw,
+__device__ __forceinline__ void fft_lanes_p(float2 (&v)[N2], int n1, float2* z, const float2* tw2,
                                             unsigned gmask) {
   constexpr int ZS = Xchg<N1, N2>::ZS, H = Xchg<N1, N2>::H;
   DftP<N2, NZ>::run(v);
 #pragma unroll
-  for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
+  for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw2[k2 * N1 + n1]);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) z[k2 * ZS + n1] = v[k2];
   __syncwarp(gmask);

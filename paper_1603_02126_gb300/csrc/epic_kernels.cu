@@ -301,12 +301,13 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
   float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][WS] grid window
   float2* Tt = Wg + A.rows_alloc * WS;                 // [N][rs] row spectra, transposed, swizzled
   float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
-  float2* tw = Z + GROUPS * G::ZG;                     // [N] twiddles
+  float2* tw = Z + GROUPS * G::ZG;                     // [N2][N1] twiddles
   float2* pixs = tw + N;                               // calibrator pixel
 
   const int tid = threadIdx.x;
   float2* zg = Z + (tid / N1) * G::ZG;
-  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
+  // twiddles ordered [k2][n1]: e^{+2 pi i n1 k2 / N}
+  for (int i = tid; i < N; i += BT) tw[i] = A.twid[(i % N1) * (i / N1)];
   for (int i = tid; i < A.rows_alloc * WS; i += BT) Wg[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
