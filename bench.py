@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused image launch
 # on this workload, with the sha256 (first 12 hex) of the kernel source it
 # was taken at; ignored when the kernel source has changed since.
-TRAFFIC = {"kernel_sha": "c8dfb121f750", "bytes_per_launch": 183435520}
+TRAFFIC = {"kernel_sha": "19c61e84bcf7", "bytes_per_launch": 183260160}
 
 
 def kernel_sha() -> str:
@@ -335,6 +335,62 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
     return out
 
 
+def profile_case(name):
+    """One untimed workload per name, the target of the ncu captures kept in
+    profiles/ (the plan, data and launch shapes of the timed forms)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1603_02126_gb300 import Plan
+    if name == "fused_lwa":            # headline interval, fused kernel
+        w = synth.workload("lwa")
+        d = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                     w["noise_power"], w["lsb"], seed=1)
+        p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"], path="fused")
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        img = p.image(d)
+        p.update()
+        p.image(d, img)
+        p.update()
+    elif name == "tc_compact":         # FP16 tensor-core form, Na=1024 / N=256, 256 samples
+        w = synth.workload("compact1024", n_time=256)
+        d = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:100], 256,
+                                     w["noise_power"], w["lsb"], seed=2)
+        p = Plan(w["ant_xy"], w["freqs"], 256, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"], path="unfused", precision="fp16", workspace_bytes=4 << 30)
+        img = p.image(d)
+        p.image(d, img)
+    elif name == "unfused_lwa":        # plain unfused path, LWA-like array, 1000 samples
+        w = synth.workload("lwa", n_time=1000)
+        d = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                     w["noise_power"], w["lsb"], seed=1)
+        p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"], path="unfused", workspace_bytes=4 << 30)
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        img = p.image(d)
+        p.update()
+        p.image(d, img)
+        p.update()
+    elif name == "grad_lwa":           # differentiation form, 16 channels, 1024 samples
+        from paper_1603_02126_gb300.autograd import EpicImageFn, chi2
+        w = synth.workload("lwa_diff", n_time=1024)
+        v = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:50], w["n_time"],
+                                     w["noise_power"], w["lsb"], seed=4)
+        mf = torch.from_numpy(synth.model_frames_c64(w["ant_xy"], w["freqs"], w["model"])).cuda()
+        pm = Plan(w["ant_xy"], w["freqs"], 128, 0.5, input="c64")
+        M = pm.image(mf) * mf.shape[0]
+        p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"])
+        for _ in range(2):
+            g = torch.from_numpy(w["gains"]).cuda().requires_grad_(True)
+            chi2(EpicImageFn.apply(g, v, p), M).backward()
+    else:
+        raise SystemExit(f"unknown case {name}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "ok": True}))
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, bounded samples."""
     if rank != 0:
@@ -382,6 +438,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision / batching / differentiation forms")
+    ap.add_argument("--case", default=None,
+                    help="run one untimed profiling workload (fused_lwa, tc_compact, unfused_lwa, "
+                         "grad_lwa) and exit")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()
@@ -392,6 +451,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case:
+        profile_case(args.case)
         return
 
     import torch
