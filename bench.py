@@ -126,6 +126,21 @@ def make_inputs(device, n_time=None):
     return w, volt
 
 
+def aggregate_ranks(total_ms, frames_per_rank, steps, dist=None, device=None):
+    """Whole-job figures: the slowest rank's time bounds the job (every rank
+    images its own channels, so no data moves between ranks); value = all
+    ranks' frames per second.  Returns (ms_per_step, value, world)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, frames_per_rank * world / (ms_per_step / 1e3), world
+
+
 def cpu_baseline(w, volt_cpu, budget_s=15.0):
     """The FP64 oracle as it stands, one channel of the same interval, on as
     many frames as fit the time budget (frames/s)."""
@@ -512,13 +527,9 @@ def main():
     clk = clocks.stop()
     held = plan.sync()
     total_ms = float(np.sum(step_ms))
+    ms_per_step, value, _ = aggregate_ranks(total_ms, frames, args.steps, dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = frames * world / (ms_per_step / 1e3)
 
     # EPICal increment: the same interval without the correlation
     plain = Plan(w["ant_xy"], w["freqs"], N, w["cell"], support=K, param=w["kernel_sigma"],
