@@ -400,6 +400,17 @@ def profile_case(name):
         for _ in range(2):
             g = torch.from_numpy(w["gains"]).cuda().requires_grad_(True)
             chi2(EpicImageFn.apply(g, v, p), M).backward()
+    elif name == "hex_unfused":        # Na=2048 hex, N=512, 128 samples, plain unfused path
+        w = synth.workload("hex2048", n_time=128)
+        v = synth.voltages_c64_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                     w["noise_power"], seed=3)
+        p = Plan(w["ant_xy"], w["freqs"], 512, 0.5, support=3, param=0.5, input="c64",
+                 path="unfused", workspace_bytes=8 << 30)
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        img = p.image(v)
+        p.update()
+        p.image(v, img)
+        p.update()
     else:
         raise SystemExit(f"unknown case {name}")
     torch.cuda.synchronize()
@@ -455,7 +466,7 @@ def main():
                     help="skip the precision / batching / differentiation forms")
     ap.add_argument("--case", default=None,
                     help="run one untimed profiling workload (fused_lwa, tc_compact, unfused_lwa, "
-                         "grad_lwa) and exit")
+                         "grad_lwa, hex_unfused) and exit")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()

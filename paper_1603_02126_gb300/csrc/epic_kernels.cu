@@ -153,10 +153,16 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
         ecur[i] = make_float2(e.x * vs, e.y * vs);
       }
     }
+    int ia = tid % Na, idy = tid / Na;                  // item (antenna, stencil row)
     for (int it = tid; it < items_pad; it += BT) {
       const bool in = it < items;
-      const int a = in ? it % Na : 0;
-      const int dy = in ? it / Na : 0;
+      const int a = in ? ia : 0;
+      const int dy = in ? idy : 0;
+      ia += BT;                                            // next item of this thread
+      while (ia >= Na) {
+        ia -= Na;
+        ++idy;
+      }
       const int c0 = in ? __ldg(cellf + a) : -1;
       const bool valid = c0 >= 0;
       float2 ec = make_float2(0.f, 0.f);
@@ -220,25 +226,42 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
 #pragma unroll
       for (int j = 0; j < NZ; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
       fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
+      if constexpr (N1 % 8 == 0) {
+        // kx = n1 + N1 h + N2 k1 = n1 (mod 8): one swizzled row index per thread
+        float2* tb = Tt + n1 * rs + (row ^ n1);
 #pragma unroll
-      for (int h = 0; h < H; ++h)
+        for (int h = 0; h < H; ++h)
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const int kx = n1 + N1 * h + N2 * k1;
-          Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
-        }
+          for (int k1 = 0; k1 < N1; ++k1) tb[(N1 * h + N2 * k1) * rs] = v[h * N1 + k1];
+      } else {
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const int kx = n1 + N1 * h + N2 * k1;
+            Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
+          }
+      }
     }
     __syncthreads();
 
     // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
+    const int jmax = (R - n1 + N1 - 1) / N1;             // this lane's rows n1 + N1 j < R
 #pragma unroll
     for (int r = 0; r < G::COLROUNDS; ++r) {
       const int kx = g + GROUPS * r;
       float2 v[N2];
+      if constexpr (N1 % 8 == 0) {
+        // kx = g (mod 8) and (n1 + N1 j) ^ s = (n1 ^ s) + N1 j for s < 8
+        const float2* cb = Tt + kx * rs + (n1 ^ (g & 7));
 #pragma unroll
-      for (int j = 0; j < N2; ++j) {
-        const int jw = n1 + N1 * j;
-        v[j] = (j < NZ && jw < R) ? Tt[kx * rs + (jw ^ (kx & 7))] : make_float2(0.f, 0.f);
+        for (int j = 0; j < N2; ++j) v[j] = (j < NZ && j < jmax) ? cb[N1 * j] : make_float2(0.f, 0.f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const int jw = n1 + N1 * j;
+          v[j] = (j < NZ && jw < R) ? Tt[kx * rs + (jw ^ (kx & 7))] : make_float2(0.f, 0.f);
+        }
       }
       fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
 #pragma unroll

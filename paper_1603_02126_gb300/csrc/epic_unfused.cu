@@ -73,7 +73,7 @@ __global__ void grid_scatter_kernel(const UnfusedArgs A, long long t0, int nt) {
 
 // ---- row FFTs: one N1-lane group per (frame, occupied row) ----
 template <int N>
-__global__ void __launch_bounds__(kUBT) rows_fft_kernel(const UnfusedArgs A, int nt) {
+__global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) rows_fft_kernel(const UnfusedArgs A, int nt) {
   constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
   constexpr int GROUPS = kUBT / N1;
   using X = fft::Xchg<N1, N2>;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kUBT) rows_fft_kernel(const UnfusedArgs A, int
 
 // ---- column FFTs + |E|^2: unit = (channel, block of GROUPS columns, time segment) ----
 template <int N>
-__global__ void __launch_bounds__(kUBT) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
+__global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
   constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
   constexpr int GROUPS = kUBT / N1;
   constexpr int CBLK = (N + GROUPS - 1) / GROUPS;   // column blocks per channel
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kUBT) cols_fft_kernel(const UnfusedArgs A, int
   }
 }
 
-// ---- EPICal correlation: one thread per (channel, antenna) over the batch ----
+// ---- EPICal correlation: one thread per (channel, antenna, time segment) ----
 __global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
   const int Na = A.n_ant, C = A.n_chan;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,8 +179,9 @@ __global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
   const int c = i / Na, a = i % Na;
   if (__ldg(A.cell0 + i) < 0) return;
   const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+  const int tb = nt * blockIdx.y / gridDim.y, te = nt * (blockIdx.y + 1) / gridDim.y;
   float kr = 0.f, ki = 0.f, pp = 0.f;
-  for (int tl = 0; tl < nt; ++tl) {
+  for (int tl = tb; tl < te; ++tl) {
     const size_t f = static_cast<size_t>(tl) * C + c;
     const float2 p = A.pix[f];
     const float2 e0 = load_volt_u(A.volt, A.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
@@ -189,9 +190,24 @@ __global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
     ki += e.y * p.x - e.x * p.y;
     pp += e.x * e.x + e.y * e.y;
   }
-  A.kacc[i].x += kr;
-  A.kacc[i].y += ki;
-  A.pacc[i] += pp;
+  if (gridDim.y == 1) {
+    A.kacc[i].x += kr;
+    A.kacc[i].y += ki;
+    A.pacc[i] += pp;
+  } else {
+    atomicAdd(&A.kacc[i].x, static_cast<double>(kr));
+    atomicAdd(&A.kacc[i].y, static_cast<double>(ki));
+    atomicAdd(A.pacc + i, static_cast<double>(pp));
+  }
+}
+
+// Time segments for the correlation: enough blocks to fill the GPU, at
+// least 16 time samples each.
+dim3 correlate_grid(int n_chan, int n_ant, int nt, int sms) {
+  const int bx = (n_chan * n_ant + 255) / 256;
+  int sy = 1;
+  while (bx * sy < 4 * sms && nt / (2 * sy) >= 16) sy *= 2;
+  return dim3(static_cast<unsigned>(bx), static_cast<unsigned>(sy));
 }
 
 template <int N>
@@ -215,10 +231,7 @@ cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms
   const int units = base_units * segs;
   const int cb = units < sms * 4 ? units : sms * 4;
   cols_fft_kernel<N><<<cb, kUBT, 0, s>>>(a, nt, segs);
-  if (a.do_cal) {
-    const int n = a.n_chan * a.n_ant;
-    correlate_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, t0, nt);
-  }
+  if (a.do_cal) correlate_kernel<<<correlate_grid(a.n_chan, a.n_ant, nt, sms), 256, 0, s>>>(a, t0, nt);
   return cudaGetLastError();
 }
 
@@ -235,8 +248,7 @@ cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int 
 }
 
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s) {
-  const int n = a.n_chan * a.n_ant;
-  correlate_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, t0, nt);
+  correlate_kernel<<<correlate_grid(a.n_chan, a.n_ant, nt, 152), 256, 0, s>>>(a, t0, nt);
   return cudaGetLastError();
 }
 
