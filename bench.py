@@ -400,6 +400,17 @@ def profile_case(name):
         for _ in range(2):
             g = torch.from_numpy(w["gains"]).cuda().requires_grad_(True)
             chi2(EpicImageFn.apply(g, v, p), M).backward()
+    elif name == "cluster_compact":    # cluster path, Na=1024 / N=256, 64 samples
+        w = synth.workload("compact1024", n_time=64)
+        d = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:100], 64,
+                                     w["noise_power"], w["lsb"], seed=2)
+        p = Plan(w["ant_xy"], w["freqs"], 256, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"], path="cluster")
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        img = p.image(d)
+        p.update()
+        p.image(d, img)
+        p.update()
     elif name == "hex_unfused":        # Na=2048 hex, N=512, 128 samples, plain unfused path
         w = synth.workload("hex2048", n_time=128)
         v = synth.voltages_c64_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
@@ -466,7 +477,7 @@ def main():
                     help="skip the precision / batching / differentiation forms")
     ap.add_argument("--case", default=None,
                     help="run one untimed profiling workload (fused_lwa, tc_compact, unfused_lwa, "
-                         "grad_lwa, hex_unfused) and exit")
+                         "grad_lwa, hex_unfused, cluster_compact) and exit")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()

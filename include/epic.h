@@ -54,9 +54,14 @@ typedef enum { EPIC_IN_CI4 = 0, EPIC_IN_COMPLEX64 = 1 } epic_input_format;
 typedef enum { EPIC_PREC_FP32 = 0, EPIC_PREC_FP16 = 1, EPIC_PREC_BF16 = 2 } epic_precision;
 /* Kernel structure of epic_image.  FUSED: one persistent launch keeps each
  * frame in one SM (N <= 128).  UNFUSED: the plain path, grid and row
- * spectra pass through device memory in batches (N = 32..512).  AUTO picks
- * FUSED when it applies. */
-typedef enum { EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2 } epic_path;
+ * spectra pass through device memory in batches (N = 32..512).  CLUSTER:
+ * one persistent launch in which a thread-block cluster (8 CTAs for N = 256,
+ * 16 for N = 512) shares each frame through distributed shared memory.
+ * AUTO picks FUSED for N <= 128, else UNFUSED (measured faster than
+ * CLUSTER on this build). */
+typedef enum {
+  EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2, EPIC_PATH_CLUSTER = 3
+} epic_path;
 
 /* Plan description (Sec. 2.1: antenna positions, grid, kernel, channels). */
 typedef struct {

@@ -128,6 +128,36 @@ bool unfused_supported(int n);
 cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s);
 
+// Thread-block-cluster imaging for N = 256 / 512, epic_cluster.cu.
+struct ClusterArgs {
+  const void* volt;
+  int input_fmt;
+  long long n_time;
+  int n_chan, n_ant, support;
+  const int* rowcol;       // [C][Na] stencil top window row << 16 | first window column; -1 flagged
+  const int* order;        // [C][Na] unflagged antennas sorted by stencil top row
+  const int2* ranges;      // [C][CS] range of `order` whose stencils meet each CTA's rows
+  const float* wts;        // [C][Na][K*K] folded weights
+  const float2* wgain;     // [C][Na] 1/g
+  const float* vscale;     // [C] or nullptr
+  const int4* win4;        // [C] (y0, rows, x0, cols)
+  const float2* twid;      // [N]
+  const float2* pixph;     // [C] calibrator-pixel phase (window coordinates)
+  double* image;
+  double img_scale;
+  int do_cal, k0x, k0y;
+  double2* kacc;
+  double* pacc;
+  int segs, rpc_alloc, rs, grid;
+  int frames_per_step;     // frames per pair of cluster barriers (spectra slots)
+  size_t smem;
+};
+bool cluster_supported(int n);
+int cluster_size(int n);
+size_t cluster_smem_bytes(int n, int rpc_alloc, int rs, int frames_per_step);
+cudaError_t cluster_prepare(int n, size_t smem, int* clusters);
+cudaError_t launch_cluster(int n, const ClusterArgs& a, cudaStream_t s);
+
 // Reduced-precision (tensor-core column DFT) batch, epic_tc.cu.
 struct TcArgs {
   UnfusedArgs u;           // gridding inputs, grid scratch, image, pixel, EPICal sums

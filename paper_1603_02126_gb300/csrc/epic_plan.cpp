@@ -143,6 +143,11 @@ struct epic_plan_s {
   DevBuf<int> d_err;            // bounded-wait timeout flag
   alignas(64) unsigned char tm_dft[128];
   alignas(64) unsigned char tm_data[128];
+
+  // cluster path (N = 256 / 512)
+  int cs = 0, rpc_alloc = 0, clusters = 0, cl_step = 1;
+  DevBuf<int> d_rowcol, d_order;
+  DevBuf<int2> d_ranges;
 };
 
 namespace {
@@ -201,6 +206,43 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
   a.smem = p->smem;
   return a;
+}
+
+// Cluster path: one persistent launch of thread-block clusters.
+epic_status image_cluster(epic_plan_t p, const void* d_volt, long long n_time, double* d_image) {
+  epic::ClusterArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.support = p->k;
+  a.rowcol = p->d_rowcol.p;
+  a.order = p->d_order.p;
+  a.ranges = p->d_ranges.p;
+  a.wts = p->d_wts.p;
+  a.wgain = p->d_wgain.p;
+  a.vscale = p->d_vscale.p;
+  a.win4 = p->d_win4.p;
+  a.twid = p->d_twid.p;
+  a.pixph = p->d_pixph.p;
+  a.image = d_image;
+  a.img_scale = 1.0 / static_cast<double>(n_time);
+  a.do_cal = p->cal ? 1 : 0;
+  a.k0x = p->cal ? p->k0x : 0;
+  a.k0y = p->cal ? p->k0y : 0;
+  a.kacc = p->d_kacc.p;
+  a.pacc = p->d_pacc.p;
+  a.segs = choose_segments(p->nc, n_time, p->clusters, p->tune_units);
+  a.rpc_alloc = p->rpc_alloc;
+  a.rs = p->rs_fused;
+  a.frames_per_step = p->cl_step;
+  const long long units = static_cast<long long>(p->nc) * a.segs;
+  a.grid = static_cast<int>(std::min<long long>(units, p->clusters)) * p->cs;
+  a.smem = p->smem;
+  EPIC_CUDA(epic::launch_cluster(p->n, a, p->stream));
+  if (p->cal) p->frames += n_time;
+  return EPIC_OK;
 }
 
 // Plain unfused path: batches of time samples through the device scratch.
@@ -408,8 +450,13 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   for (int i = 0; i < 2 * d->n_ant; ++i)
     if (!std::isfinite(d->ant_xy_m[i])) return fail(EPIC_ERR_INVALID_ARG, "non-finite antenna position");
 
-  if (d->path != EPIC_PATH_AUTO && d->path != EPIC_PATH_FUSED && d->path != EPIC_PATH_UNFUSED)
+  if (d->path != EPIC_PATH_AUTO && d->path != EPIC_PATH_FUSED && d->path != EPIC_PATH_UNFUSED &&
+      d->path != EPIC_PATH_CLUSTER)
     return fail(EPIC_ERR_INVALID_ARG, "unknown path");
+  if (d->path == EPIC_PATH_CLUSTER &&
+      (!epic::cluster_supported(d->grid_n) || d->n_ant > 256 * epic::cluster_size(d->grid_n) ||
+       d->precision != EPIC_PREC_FP32))
+    return fail(EPIC_ERR_UNSUPPORTED, "cluster path: FP32, grid_n 256 or 512, n_ant <= 256 x cluster size");
   epic::ImageKernelShape shape{};
   const bool fused_shape = epic::image_kernel_shape(d->grid_n, &shape) && d->n_ant <= shape.max_ant;
   const bool unfused_ok = epic::unfused_supported(d->grid_n);
@@ -577,7 +624,36 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       fused = false;
     }
   }
-  if (fused) {
+  const bool want_cluster = !fused && p->precision == EPIC_PREC_FP32 && d->path == EPIC_PATH_CLUSTER &&
+                            epic::cluster_supported(N) && Na <= 256 * epic::cluster_size(N);
+  if (want_cluster) {
+    p->cs = epic::cluster_size(N);
+    p->rpc_alloc = (p->rows_alloc + p->cs - 1) / p->cs;
+    // frames per pair of cluster barriers: as many spectra slots as fit, up to 4
+    p->cl_step = 4;
+    while (p->cl_step > 1 &&
+           epic::cluster_smem_bytes(N, p->rpc_alloc, p->rs_fused, p->cl_step) > static_cast<size_t>(smem_optin))
+      --p->cl_step;
+    const size_t csm = epic::cluster_smem_bytes(N, p->rpc_alloc, p->rs_fused, p->cl_step);
+    int ncl = 0;
+    e = csm <= static_cast<size_t>(smem_optin) ? epic::cluster_prepare(N, csm, &ncl) : cudaErrorInvalidValue;
+    if (e == cudaSuccess && ncl >= 1) {
+      p->smem = csm;
+      p->clusters = ncl;
+      p->ctas = ncl * p->cs;
+      p->path = EPIC_PATH_CLUSTER;
+    } else if (d->path == EPIC_PATH_CLUSTER) {
+      delete p;
+      return e != cudaSuccess && e != cudaErrorInvalidValue ? cuda_fail(e, "cluster kernel attributes")
+                                                            : fail(EPIC_ERR_UNSUPPORTED, "cluster kernel cannot be resident");
+    } else {
+      cudaGetLastError();
+      p->cs = 0;
+    }
+  }
+  if (p->path == EPIC_PATH_CLUSTER) {
+    // tables built below with the device tables
+  } else if (fused) {
     int per_sm = 0;
     e = epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
@@ -612,6 +688,39 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
     }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
+  // cluster path: stencil (top row, first column) in window coordinates,
+  // antennas sorted by top row, and per CTA the sorted range whose stencil
+  // rows meet the CTA's row block (rows per CTA = ceil(rows / CS))
+  std::vector<int> rowcol, order;
+  std::vector<int2> ranges;
+  if (p->path == EPIC_PATH_CLUSTER) {
+    const int CS = p->cs;
+    rowcol.assign(static_cast<size_t>(C) * Na, -1);
+    order.assign(static_cast<size_t>(C) * Na, 0);
+    ranges.assign(static_cast<size_t>(C) * CS, make_int2(0, 0));
+    for (int c = 0; c < C; ++c) {
+      std::vector<std::pair<int, int>> tops;
+      for (int a = 0; a < Na; ++a) {
+        if (p->flags[a]) continue;
+        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+        const int top = p->base[ob + 1] - h - p->y0[c];
+        const int col = p->base[ob] - h - p->x0[c];
+        rowcol[static_cast<size_t>(c) * Na + a] = (top << 16) | col;
+        tops.emplace_back(top, a);
+      }
+      std::stable_sort(tops.begin(), tops.end());
+      for (size_t i = 0; i < tops.size(); ++i) order[static_cast<size_t>(c) * Na + i] = tops[i].second;
+      const int rpc = (p->rows[c] + CS - 1) / CS;
+      for (int q = 0; q < CS; ++q) {
+        const int lo_top = q * rpc - K + 1, hi_top = (q + 1) * rpc - 1;
+        int lo = 0, hi = 0;
+        while (lo < static_cast<int>(tops.size()) && tops[lo].first < lo_top) ++lo;
+        hi = lo;
+        while (hi < static_cast<int>(tops.size()) && tops[hi].first <= hi_top) ++hi;
+        ranges[static_cast<size_t>(c) * CS + q] = make_int2(lo, hi);
+      }
+    }
+  }
   std::vector<double2> gain(static_cast<size_t>(C) * Na, make_double2(1.0, 0.0));
   std::vector<float2> wgain(static_cast<size_t>(C) * Na, make_float2(1.0f, 0.0f));
 
@@ -623,7 +732,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   cudaError_t es[] = {up(p->d_cell0, cell0), up(p->d_wts, wts), up(p->d_wgain, wgain),
                       up(p->d_gain, gain), up(p->d_vscale, p->vscale), up(p->d_win, win),
                       up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
-                      up(p->d_cellf, cellf), up(p->d_pixph, pixph)};
+                      up(p->d_cellf, cellf), up(p->d_pixph, pixph), up(p->d_rowcol, rowcol),
+                      up(p->d_order, order), up(p->d_ranges, ranges)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -654,6 +764,9 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_win4.release();
   p->d_cellf.release();
   p->d_pixph.release();
+  p->d_rowcol.release();
+  p->d_order.release();
+  p->d_ranges.release();
   p->d_twid.release();
   p->d_flags.release();
   p->d_a0.release();
@@ -731,6 +844,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   const size_t img_bytes = static_cast<size_t>(p->nc) * p->n * p->n * sizeof(double);
   if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_image, 0, img_bytes, p->stream));
   if (p->precision != EPIC_PREC_FP32) return image_tc(p, d_volt, n_time, d_image);
+  if (p->path == EPIC_PATH_CLUSTER) return image_cluster(p, d_volt, n_time, d_image);
   if (p->path == EPIC_PATH_UNFUSED) return image_unfused(p, d_volt, n_time, d_image);
   const epic::ImageArgs a = fused_args(p, d_volt, n_time, d_image, 1.0 / static_cast<double>(n_time));
   EPIC_CUDA(epic::launch_image(p->n, a, p->stream));
