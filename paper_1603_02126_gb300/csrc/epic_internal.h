@@ -22,6 +22,9 @@ struct ImageArgs {
   const int2* win;         // [C] (first occupied grid row y0, occupied rows R)
   const int4* win4;        // [C] (y0, rows, x0, columns) of the occupied window
   const int* cellf;        // [C][Na] window cell (row * (N + N1) + col - x0); -1 = flagged
+  const int* gofs;         // [C][rows_alloc][N1] first gather entry of each FFT lane
+  const uint2* gent;       // gather entries (antenna << 5 | column block j, weight bits);
+                           // each lane's list sorted by j and closed by j = 31
   const float2* pixph;     // [C] (-1)^(k0x+k0y) e^{2 pi i (x0 k0x + y0 k0y)/N}
   const float2* twid;      // [N] e^{+2 pi i m / N}
   double* image;           // [C][N][N] accumulated with img_scale
@@ -53,7 +56,10 @@ int image_rs_fused(int rows_alloc);
 size_t adjoint_smem_bytes(int n, int rows_alloc, int rs);
 // Row stride of the fused kernel's grid window, N + N1.
 int image_window_stride(int n);
-size_t image_smem_bytes(int n, int rows_alloc, int rs);
+size_t image_smem_bytes(int n, int n_ant, int rs);
+// Lanes per 1-D FFT (N1) of the fused kernel: window column x is entry
+// block j = x / N1 of lane x % N1.
+int image_fft_lanes(int n);
 // Opt in to the shared memory and report resident CTAs per SM.
 cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas_per_sm);
 cudaError_t launch_image(int n, const ImageArgs& a, cudaStream_t s);

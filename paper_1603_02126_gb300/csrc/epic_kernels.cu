@@ -90,36 +90,67 @@ __device__ __forceinline__ float2 load_volt(const ImageArgs& A, long long t, int
   return __ldg(static_cast<const float2*>(A.volt) + idx);
 }
 
+// Raw voltage of antenna a in frame t, fetched one frame ahead: the 4-bit
+// byte (ci4) or the complex64 value, unpacked only when it is used.
+struct RawVolt {
+  unsigned b;
+  float2 f;
+};
+
+__device__ __forceinline__ RawVolt fetch_volt(const ImageArgs& A, long long t, int c, int a) {
+  const size_t idx = (static_cast<size_t>(t) * A.n_chan + c) * A.n_ant + a;
+  RawVolt r;
+  if (A.input_fmt == 0) {
+    r.b = __ldg(static_cast<const unsigned char*>(A.volt) + idx);
+    r.f = make_float2(0.f, 0.f);
+  } else {
+    r.b = 0;
+    r.f = __ldg(static_cast<const float2*>(A.volt) + idx);
+  }
+  return r;
+}
+
+__device__ __forceinline__ float2 unpack_volt(const ImageArgs& A, const RawVolt& r, float vs) {
+  if (A.input_fmt == 0) {
+    const int re = static_cast<int>(r.b << 24) >> 28;
+    const int im = static_cast<int>(r.b << 28) >> 28;
+    return make_float2(static_cast<float>(re) * vs, static_cast<float>(im) * vs);
+  }
+  return make_float2(r.f.x * vs, r.f.y * vs);
+}
+
 // One work unit (channel c, frames [t0, t1)) of the fused kernel, for an
 // occupied window of at most N1 * NZ rows and columns: the grid is kept in
 // window coordinates (first occupied row and column at 0), which only
 // changes the phase of each image pixel, so every 1-D FFT has at most NZ
 // non-zero inputs per lane and uses the pruned first-stage DFT.
+//
+// Gridding (Eq. 9) is a gather: the array layout is fixed for the plan, so
+// the host lists, for every FFT lane (window row, lane n1), the taps that
+// land on the lane's columns n1 + N1 j as entries (antenna << 5 | j, weight),
+// sorted by j and closed by a sentinel (j = 31).  Each frame the lane sums
+// w * E'_a over its list straight into its FFT inputs; E'_a = E_a / g_a
+// (Eq. 8) sits in shared memory, computed once per antenna while the
+// previous frame's column FFTs run.  No atomics, and the sum order is fixed.
 template <int N, int MAXA, int NZ>
 __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long t0, long long t1,
-                                           float2* Wg, float2* Tt, float2* zg, const float2* tw,
-                                           float2* pixs) {
+                                           float2* Tt, float2* zg, const float2* tw, float2* pixs,
+                                           float2* Es) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
-  constexpr int WS = N + N1;                           // grid-window row stride
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
   const int g = tid / N1;
   const int n1 = tid % N1;
-  const unsigned gmask = fft::group_mask<N1>(lane);
+  const unsigned gmask = fft::group_mask<N1>(tid & 31);
   const int Na = A.n_ant;
-  const int K = A.support;
-  const int KK = K * K;
-  const int items = K * Na;
-  const int items_pad = ((items + BT - 1) / BT) * BT;
   const int rs = A.rs;
 
   const int4 wn = __ldg(A.win4 + c);                   // (y0, rows, x0, cols)
   const int R = wn.y;
   const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
-  const int* cellf = A.cellf + static_cast<size_t>(c) * Na;
-  const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
   const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
+  const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
+  const uint2* gent = A.gent;
 
   // calibrator pixel: column round, group, lane and register slot, phase
   const int pr = A.k0x / GROUPS, pg = A.k0x % GROUPS;
@@ -132,82 +163,34 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   float acc[G::NACC];
 #pragma unroll
   for (int i = 0; i < G::NACC; ++i) acc[i] = 0.f;
-  float2 kac[MAXA], ecur[MAXA];
+  float2 kac[MAXA], ecur[MAXA], eprev[MAXA];
   float pac[MAXA];
 #pragma unroll
   for (int i = 0; i < MAXA; ++i) {
     kac[i] = make_float2(0.f, 0.f);
-    ecur[i] = make_float2(0.f, 0.f);
+    eprev[i] = make_float2(0.f, 0.f);
     pac[i] = 0.f;
+    // frame t0: raw voltages (for the correlation) and E' = E / g
+    const int a = tid + BT * i;
+    ecur[i] = make_float2(0.f, 0.f);
+    if (a < Na) {
+      ecur[i] = unpack_volt(A, fetch_volt(A, t0, c, a), vs);
+      Es[a] = cmul(ecur[i], __ldg(wg + a));
+    }
   }
+  __syncthreads();
 
   for (long long t = t0; t < t1; ++t) {
-    // ---- A: raw voltages for the correlation, then gain + scatter ----
-    float2 eprev[MAXA];
+    const bool more = t + 1 < t1;
+    // next frame's voltages: issued now, used after the row pass
+    RawVolt nxt[MAXA];
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
-      eprev[i] = ecur[i];
       const int a = tid + BT * i;
-      if (A.do_cal && a < Na) {
-        const float2 e = load_volt(A, t, c, a);
-        ecur[i] = make_float2(e.x * vs, e.y * vs);
-      }
+      nxt[i] = (more && a < Na) ? fetch_volt(A, t + 1, c, a) : RawVolt{0u, make_float2(0.f, 0.f)};
     }
-    int ia = tid % Na, idy = tid / Na;                  // item (antenna, stencil row)
-    for (int it = tid; it < items_pad; it += BT) {
-      const bool in = it < items;
-      const int a = in ? ia : 0;
-      const int dy = in ? idy : 0;
-      ia += BT;                                            // next item of this thread
-      while (ia >= Na) {
-        ia -= Na;
-        ++idy;
-      }
-      const int c0 = in ? __ldg(cellf + a) : -1;
-      const bool valid = c0 >= 0;
-      float2 ec = make_float2(0.f, 0.f);
-      if (valid) {
-        const float2 e = load_volt(A, t, c, a);
-        ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
-      }
-      const int rowcell = valid ? c0 + dy * WS : -1 - lane;
-      const unsigned peers = __match_any_sync(kFull, rowcell);
-      const bool dup = __popc(peers) > 1;
-      const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
-      if (!__any_sync(kFull, dup)) {
-        if (valid) {
-          for (int dx = 0; dx < K; ++dx) {
-            const float w = __ldg(wrow + dx);
-            atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
-            atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
-          }
-        }
-      } else {
-        // lanes sharing a cell: the lowest lane adds the group's sum
-        const int leader = __ffs(peers) - 1;
-        for (int dx = 0; dx < K; ++dx) {
-          const float w = valid ? __ldg(wrow + dx) : 0.f;
-          const float vx = w * ec.x, vy = w * ec.y;
-          float sx = 0.f, sy = 0.f;
-#pragma unroll
-          for (int src = 0; src < 32; ++src) {
-            const float ox = __shfl_sync(kFull, vx, src);
-            const float oy = __shfl_sync(kFull, vy, src);
-            if ((peers >> src) & 1u) {
-              sx += ox;
-              sy += oy;
-            }
-          }
-          if (valid && lane == leader) {
-            atomicAdd(&Wg[rowcell + dx].x, sx);
-            atomicAdd(&Wg[rowcell + dx].y, sy);
-          }
-        }
-      }
-    }
-    __syncthreads();
 
-    // ---- B: correlation of the previous frame, then row FFTs ----
+    // ---- B: correlation of the previous frame, then gather + row FFTs ----
     if (A.do_cal && t > t0) {
       const float2 p = pixs[0];
 #pragma unroll
@@ -220,11 +203,22 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
     }
     for (int row = g; row < R; row += GROUPS) {
       float2 v[N2];
-      float2* wr = Wg + row * WS;
+      int e = __ldg(gofs + row * N1 + n1);
+      uint2 en = __ldg(gent + e);
 #pragma unroll
-      for (int j = 0; j < N2; ++j) v[j] = (j < NZ) ? wr[n1 + N1 * j] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < NZ; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < N2; ++j) {
+        float2 sum = make_float2(0.f, 0.f);
+        if (j < NZ) {
+          while ((en.x & 31u) == static_cast<unsigned>(j)) {
+            const float2 x = Es[en.x >> 5];
+            const float w = __uint_as_float(en.y);
+            sum.x = fmaf(w, x.x, sum.x);
+            sum.y = fmaf(w, x.y, sum.y);
+            en = __ldg(gent + (++e));
+          }
+        }
+        v[j] = sum;
+      }
       fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
       if constexpr (N1 % 8 == 0) {
         // kx = n1 + N1 h + N2 k1 = n1 (mod 8): one swizzled row index per thread
@@ -244,6 +238,17 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
       }
     }
     __syncthreads();
+
+    // ---- next frame's E' (the row pass has finished reading Es) ----
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
+      eprev[i] = ecur[i];
+      if (more && a < Na) {
+        ecur[i] = unpack_volt(A, nxt[i], vs);
+        Es[a] = cmul(ecur[i], __ldg(wg + a));
+      }
+    }
 
     // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
     const int jmax = (R - n1 + N1 - 1) / N1;             // this lane's rows n1 + N1 j < R
@@ -272,8 +277,8 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
           if (q == pslot) pixs[0] = cmul(v[q], pph);
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   // correlation of the unit's last frame
   if (A.do_cal) {
@@ -301,10 +306,11 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
       }
   }
   if (A.do_cal) {
+    const int* cellf = A.cellf + static_cast<size_t>(c) * Na;
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
       const int a = tid + BT * i;
-      if (a < Na && cellf[a] >= 0) {
+      if (a < Na && __ldg(cellf + a) >= 0) {
         const size_t o = static_cast<size_t>(c) * Na + a;
         atomicAdd(&A.kacc[o].x, static_cast<double>(kac[i].x));
         atomicAdd(&A.kacc[o].y, static_cast<double>(kac[i].y));
@@ -312,26 +318,25 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
       }
     }
   }
+  __syncthreads();                                     // Es and pixs are reused by the next unit
 }
 
 template <int N, int MAXA>
 __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS;
-  constexpr int WS = N + N1;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][WS] grid window
-  float2* Tt = Wg + A.rows_alloc * WS;                 // [N][rs] row spectra, transposed, swizzled
+  float2* Tt = reinterpret_cast<float2*>(smem_raw);   // [N][rs] row spectra, transposed, swizzled
   float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
   float2* tw = Z + GROUPS * G::ZG;                     // [N2][N1] twiddles
   float2* pixs = tw + N;                               // calibrator pixel
+  float2* Es = pixs + 2;                               // [Na] gain-corrected voltages
 
   const int tid = threadIdx.x;
   float2* zg = Z + (tid / N1) * G::ZG;
   // twiddles ordered [k2][n1]: e^{+2 pi i n1 k2 / N}
   for (int i = tid; i < N; i += BT) tw[i] = A.twid[(i % N1) * (i / N1)];
-  for (int i = tid; i < A.rows_alloc * WS; i += BT) Wg[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const long long T = A.n_time;
@@ -345,11 +350,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
     const int4 wn = __ldg(A.win4 + c);
     const int span = wn.y > wn.w ? wn.y : wn.w;          // occupied rows / columns
     if (span <= N1 * (N2 / 4))
-      fused_unit<N, MAXA, N2 / 4>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
+      fused_unit<N, MAXA, N2 / 4>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
     else if (span <= N1 * (N2 / 2))
-      fused_unit<N, MAXA, N2 / 2>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
+      fused_unit<N, MAXA, N2 / 2>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
     else
-      fused_unit<N, MAXA, N2>(A, c, t0, t1, Wg, Tt, zg, tw, pixs);
+      fused_unit<N, MAXA, N2>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
   }
 }
 
@@ -770,18 +775,29 @@ int image_rs_fused(int rows_alloc) {
   return rs;
 }
 
-size_t image_smem_bytes(int n, int rows_alloc, int rs) {
-  int groups = 0, zg = 0, n1 = 0;
+size_t image_smem_bytes(int n, int n_ant, int rs) {
+  int groups = 0, zg = 0;
   switch (n) {
-    case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; n1 = Geo<16>::N1; break;
-    case 32: groups = Geo<32>::GROUPS; zg = Geo<32>::ZG; n1 = Geo<32>::N1; break;
-    case 64: groups = Geo<64>::GROUPS; zg = Geo<64>::ZG; n1 = Geo<64>::N1; break;
-    case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; n1 = Geo<128>::N1; break;
+    case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
+    case 32: groups = Geo<32>::GROUPS; zg = Geo<32>::ZG; break;
+    case 64: groups = Geo<64>::GROUPS; zg = Geo<64>::ZG; break;
+    case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
     default: return 0;
   }
-  const size_t elems = static_cast<size_t>(rows_alloc) * (n + n1) + static_cast<size_t>(n) * rs +
-                       static_cast<size_t>(groups) * zg + n + 2;
+  // spectra [N][rs], exchange, twiddles, calibrator pixel, E' [Na]
+  const size_t elems = static_cast<size_t>(n) * rs + static_cast<size_t>(groups) * zg + n + 2 +
+                       static_cast<size_t>(n_ant);
   return elems * sizeof(float2);
+}
+
+int image_fft_lanes(int n) {
+  switch (n) {
+    case 16: return Geo<16>::N1;
+    case 32: return Geo<32>::N1;
+    case 64: return Geo<64>::N1;
+    case 128: return Geo<128>::N1;
+    default: return 0;
+  }
 }
 
 cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas) {

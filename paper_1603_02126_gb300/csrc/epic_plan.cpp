@@ -88,6 +88,8 @@ struct epic_plan_s {
   DevBuf<int2> d_win;           // [C]
   DevBuf<int4> d_win4;          // [C] (y0, rows, x0, cols) for the fused kernel
   DevBuf<int> d_cellf;          // [C][Na] fused-kernel window cell of tap (0,0)
+  DevBuf<int> d_gofs;           // [C][rows_alloc][N1] fused gather: first entry per FFT lane
+  DevBuf<uint2> d_gent;         // fused gather entries (antenna << 5 | j, weight bits)
   DevBuf<float2> d_pixph;       // [C] calibrator-pixel phase in window coordinates
   std::vector<int> x0, cols;    // [C] first occupied column, occupied columns
   int rs_fused = 0;
@@ -184,6 +186,8 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.support = p->k;
   a.cell0 = p->d_cell0.p;
   a.cellf = p->d_cellf.p;
+  a.gofs = p->d_gofs.p;
+  a.gent = p->d_gent.p;
   a.wts = p->d_wts.p;
   a.wgain = p->d_wgain.p;
   a.vscale = p->d_vscale.p;
@@ -612,7 +616,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   }
   p->rs_fused = epic::image_rs_fused(p->rows_alloc);
   if (fused) {
-    p->smem = epic::image_smem_bytes(N, p->rows_alloc, p->rs_fused);
+    p->smem = epic::image_smem_bytes(N, Na, p->rs_fused);
     if (p->smem > static_cast<size_t>(smem_optin)) {
       const std::string msg = "array footprint needs " + std::to_string(p->smem) +
                               " B of shared memory in the fused kernel (limit " +
@@ -687,6 +691,48 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       const int bx = p->base[ob], by = p->base[ob + 1];
       cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
     }
+  // fused path: per FFT lane (window row r, lane n1 = x mod N1) the taps on
+  // its columns x = n1 + N1 j, sorted by j, then a sentinel entry (j = 31)
+  std::vector<int> gofs;
+  std::vector<uint2> gent;
+  if (p->path == EPIC_PATH_FUSED) {
+    const int N1 = epic::image_fft_lanes(N);
+    const int RA = p->rows_alloc;
+    gofs.assign(static_cast<size_t>(C) * RA * N1, 0);
+    std::vector<std::vector<std::pair<unsigned, float>>> lists(static_cast<size_t>(RA) * N1);
+    for (int c = 0; c < C; ++c) {
+      for (auto& l : lists) l.clear();
+      for (int a = 0; a < Na; ++a) {
+        if (p->flags[a]) continue;
+        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+        const int r0 = p->base[ob + 1] - h - p->y0[c], x0w = p->base[ob] - h - p->x0[c];
+        const float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
+        for (int dy = 0; dy < K; ++dy)
+          for (int dx = 0; dx < K; ++dx) {
+            const float w = wf[dy * K + dx];
+            if (w == 0.0f) continue;
+            const int x = x0w + dx;
+            lists[static_cast<size_t>(r0 + dy) * N1 + x % N1].emplace_back(
+                (static_cast<unsigned>(a) << 5) | static_cast<unsigned>(x / N1), w);
+          }
+      }
+      for (int li = 0; li < RA * N1; ++li) {
+        auto& l = lists[li];
+        std::stable_sort(l.begin(), l.end(), [](const std::pair<unsigned, float>& u,
+                                                const std::pair<unsigned, float>& v) {
+          return (u.first & 31u) < (v.first & 31u);
+        });
+        gofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(gent.size());
+        for (const auto& en : l) {
+          uint2 q;
+          q.x = en.first;
+          std::memcpy(&q.y, &en.second, sizeof(float));
+          gent.push_back(q);
+        }
+        gent.push_back(make_uint2(31u, 0u));
+      }
+    }
+  }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
   // cluster path: stencil (top row, first column) in window coordinates,
   // antennas sorted by top row, and per CTA the sorted range whose stencil
@@ -733,7 +779,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                       up(p->d_gain, gain), up(p->d_vscale, p->vscale), up(p->d_win, win),
                       up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
                       up(p->d_cellf, cellf), up(p->d_pixph, pixph), up(p->d_rowcol, rowcol),
-                      up(p->d_order, order), up(p->d_ranges, ranges)};
+                      up(p->d_order, order), up(p->d_ranges, ranges), up(p->d_gofs, gofs),
+                      up(p->d_gent, gent)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -763,6 +810,8 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_win.release();
   p->d_win4.release();
   p->d_cellf.release();
+  p->d_gofs.release();
+  p->d_gent.release();
   p->d_pixph.release();
   p->d_rowcol.release();
   p->d_order.release();
