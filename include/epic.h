@@ -57,10 +57,15 @@ typedef enum { EPIC_PREC_FP32 = 0, EPIC_PREC_FP16 = 1, EPIC_PREC_BF16 = 2 } epic
  * spectra pass through device memory in batches (N = 32..512).  CLUSTER:
  * one persistent launch in which a thread-block cluster (8 CTAs for N = 256,
  * 16 for N = 512) shares each frame through distributed shared memory.
- * AUTO picks FUSED for N <= 128, else UNFUSED (measured faster than
- * CLUSTER on this build). */
+ * PIPED: the fused path in warp-specialised form (N = 64 or 128, Na <= 512):
+ * producer warps grid and row-transform frame t + 1 while consumer warps
+ * column-transform frame t, handing frames over through two shared-memory
+ * slots (FUSED keeps the form with two CTA barriers per frame, measured
+ * faster on this build).  AUTO picks FUSED for N <= 128, else UNFUSED
+ * (measured faster than CLUSTER on this build). */
 typedef enum {
-  EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2, EPIC_PATH_CLUSTER = 3
+  EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2, EPIC_PATH_CLUSTER = 3,
+  EPIC_PATH_PIPED = 4
 } epic_path;
 
 /* Plan description (Sec. 2.1: antenna positions, grid, kernel, channels). */
@@ -93,7 +98,7 @@ typedef struct {
   size_t smem_bytes;           /* dynamic shared memory of the image kernel */
   long long frames_pending;    /* frames correlated since the last update */
   long long iteration;         /* completed EPICal updates */
-  int path;                    /* epic_path in use (FUSED or UNFUSED) */
+  int path;                    /* epic_path in use (never AUTO) */
   int batch_time;              /* UNFUSED: time samples per batch (0 before use) */
 } epic_plan_info;
 

@@ -18,7 +18,7 @@ STATUS_NAMES = {
 EPIC_KERNEL_GAUSSIAN, EPIC_KERNEL_TOPHAT = 0, 1
 EPIC_IN_CI4, EPIC_IN_COMPLEX64 = 0, 1
 EPIC_PREC_FP32, EPIC_PREC_FP16, EPIC_PREC_BF16 = 0, 1, 2
-EPIC_PATH_AUTO, EPIC_PATH_FUSED, EPIC_PATH_UNFUSED, EPIC_PATH_CLUSTER = 0, 1, 2, 3
+EPIC_PATH_AUTO, EPIC_PATH_FUSED, EPIC_PATH_UNFUSED, EPIC_PATH_CLUSTER, EPIC_PATH_PIPED = 0, 1, 2, 3, 4
 
 # every exported entry point, as declared in include/epic.h
 EXPORTS = [

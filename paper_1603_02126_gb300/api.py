@@ -17,7 +17,7 @@ from ._binding import EpicError  # noqa: F401
 _KERNELS = {"gaussian": B.EPIC_KERNEL_GAUSSIAN, "tophat": B.EPIC_KERNEL_TOPHAT}
 _INPUTS = {"ci4": B.EPIC_IN_CI4, "c64": B.EPIC_IN_COMPLEX64}
 _PATHS = {"auto": B.EPIC_PATH_AUTO, "fused": B.EPIC_PATH_FUSED, "unfused": B.EPIC_PATH_UNFUSED,
-          "cluster": B.EPIC_PATH_CLUSTER}
+          "cluster": B.EPIC_PATH_CLUSTER, "piped": B.EPIC_PATH_PIPED}
 
 
 def _torch():

@@ -132,16 +132,17 @@ __device__ __forceinline__ float2 unpack_volt(const ImageArgs& A, const RawVolt&
 // w * E'_a over its list straight into its FFT inputs; E'_a = E_a / g_a
 // (Eq. 8) sits in shared memory, computed once per antenna while the
 // previous frame's column FFTs run.  No atomics, and the sum order is fixed.
-template <int N, int MAXA, int NZ>
+template <int N, int MAXA, int NZ, bool TS>
 __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long t0, long long t1,
                                            float2* Tt, float2* zg, const float2* tw, float2* pixs,
-                                           float2* Es) {
+                                           float2* Es, int* sgofs, uint2* sgent) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
   const int tid = threadIdx.x;
   const int g = tid / N1;
   const int n1 = tid % N1;
-  const unsigned gmask = fft::group_mask<N1>(tid & 31);
+  constexpr int kGroupsPerWarp = 32 / N1;
+  constexpr bool kPadded = NZ < N2;                    // spectra rows padded to N1 * NZ
   const int Na = A.n_ant;
   const int rs = A.rs;
 
@@ -149,8 +150,16 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   const int R = wn.y;
   const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
   const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
+  // gather table of the channel: copied to shared memory for the unit (TS),
+  // else read through L1
+  const int gb = __ldg(A.gbase + c);
   const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
-  const uint2* gent = A.gent;
+  const uint2* gent = A.gent + gb;
+  if constexpr (TS) {
+    const int gn = __ldg(A.gbase + c + 1) - gb;
+    for (int i = tid; i < gn; i += BT) sgent[i] = __ldg(gent + i);
+    for (int i = tid; i < R * N1; i += BT) sgofs[i] = __ldg(gofs + i);
+  }
 
   // calibrator pixel: column round, group, lane and register slot, phase
   const int pr = A.k0x / GROUPS, pg = A.k0x % GROUPS;
@@ -159,6 +168,9 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   const int pslot = (pq % H) * N1 + pq / H;
   const bool pix_owner = A.do_cal && g == pg && n1 == pn1;
   const float2 pph = A.do_cal ? __ldg(A.pixph + c) : make_float2(1.f, 0.f);
+
+  // spectra buffer cleared: rows R .. N1 NZ - 1 are read by the column pass
+  for (int i = tid; i < N * rs; i += BT) Tt[i] = make_float2(0.f, 0.f);
 
   float acc[G::NACC];
 #pragma unroll
@@ -182,12 +194,15 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
 
   for (long long t = t0; t < t1; ++t) {
     const bool more = t + 1 < t1;
-    // next frame's voltages: issued now, used after the row pass
-    RawVolt nxt[MAXA];
-#pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      const int a = tid + BT * i;
-      nxt[i] = (more && a < Na) ? fetch_volt(A, t + 1, c, a) : RawVolt{0u, make_float2(0.f, 0.f)};
+    // next frame's voltages: pulled into L1 now (no register waits on
+    // them), loaded after the row pass
+    if (more) {
+      const size_t esz = A.input_fmt == 0 ? 1 : sizeof(float2);
+      const size_t off = (static_cast<size_t>(t + 1) * A.n_chan + c) * Na * esz;
+      const uintptr_t lo = (reinterpret_cast<uintptr_t>(A.volt) + off) & ~static_cast<uintptr_t>(127);
+      const uintptr_t hi = reinterpret_cast<uintptr_t>(A.volt) + off + Na * esz;
+      for (uintptr_t q = lo + static_cast<uintptr_t>(tid) * 128; q < hi; q += BT * 128)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
     }
 
     // ---- B: correlation of the previous frame, then gather + row FFTs ----
@@ -201,56 +216,67 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
         pac[i] += e.x * e.x + e.y * e.y;
       }
     }
-    for (int row = g; row < R; row += GROUPS) {
+    // whole warps step through the rows together (full-warp syncs in the
+    // FFT exchange); lanes past the last row transform zeros and store nothing
+    for (int rb = g - g % kGroupsPerWarp; rb < R; rb += GROUPS) {
+      const int row = rb + g % kGroupsPerWarp;
+      const bool live = row < R;
       float2 v[N2];
-      int e = __ldg(gofs + row * N1 + n1);
-      uint2 en = __ldg(gent + e);
 #pragma unroll
-      for (int j = 0; j < N2; ++j) {
-        float2 sum = make_float2(0.f, 0.f);
-        if (j < NZ) {
+      for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
+      if (live) {
+        int e = TS ? sgofs[row * N1 + n1] : __ldg(gofs + row * N1 + n1);
+        uint2 en = TS ? sgent[e] : __ldg(gent + e);
+#pragma unroll
+        for (int j = 0; j < NZ; ++j) {
+          float2 sum = make_float2(0.f, 0.f);
           while ((en.x & 31u) == static_cast<unsigned>(j)) {
             const float2 x = Es[en.x >> 5];
             const float w = __uint_as_float(en.y);
             sum.x = fmaf(w, x.x, sum.x);
             sum.y = fmaf(w, x.y, sum.y);
-            en = __ldg(gent + (++e));
+            ++e;
+            en = TS ? sgent[e] : __ldg(gent + e);
           }
+          v[j] = sum;
         }
-        v[j] = sum;
       }
-      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
-      if constexpr (N1 % 8 == 0) {
-        // kx = n1 + N1 h + N2 k1 = n1 (mod 8): one swizzled row index per thread
-        float2* tb = Tt + n1 * rs + (row ^ n1);
+      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, kFull);
+      if (live) {
+        if constexpr (N1 % 8 == 0) {
+          // kx = n1 + N1 h + N2 k1 = n1 (mod 8): one swizzled row index per thread
+          float2* tb = Tt + n1 * rs + (row ^ n1);
 #pragma unroll
-        for (int h = 0; h < H; ++h)
+          for (int h = 0; h < H; ++h)
 #pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) tb[(N1 * h + N2 * k1) * rs] = v[h * N1 + k1];
-      } else {
+            for (int k1 = 0; k1 < N1; ++k1) tb[(N1 * h + N2 * k1) * rs] = v[h * N1 + k1];
+        } else {
 #pragma unroll
-        for (int h = 0; h < H; ++h)
+          for (int h = 0; h < H; ++h)
 #pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const int kx = n1 + N1 * h + N2 * k1;
-            Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
-          }
+            for (int k1 = 0; k1 < N1; ++k1) {
+              const int kx = n1 + N1 * h + N2 * k1;
+              Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
+            }
+        }
       }
     }
     __syncthreads();
 
-    // ---- next frame's E' (the row pass has finished reading Es) ----
+    // next frame's voltages and gains, used after the column pass
+    RawVolt nxt[MAXA];
+    float2 gnx[MAXA];
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
       const int a = tid + BT * i;
-      eprev[i] = ecur[i];
-      if (more && a < Na) {
-        ecur[i] = unpack_volt(A, nxt[i], vs);
-        Es[a] = cmul(ecur[i], __ldg(wg + a));
-      }
+      const bool ld = more && a < Na;
+      nxt[i] = ld ? fetch_volt(A, t + 1, c, a) : RawVolt{0u, make_float2(0.f, 0.f)};
+      gnx[i] = ld ? __ldg(wg + a) : make_float2(0.f, 0.f);
     }
 
     // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
+    // (pruned forms: spectra rows R .. N1 NZ - 1 hold zeros, so the loads
+    // need no bounds test; the full form reads rows < R only)
     const int jmax = (R - n1 + N1 - 1) / N1;             // this lane's rows n1 + N1 j < R
 #pragma unroll
     for (int r = 0; r < G::COLROUNDS; ++r) {
@@ -260,21 +286,33 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
         // kx = g (mod 8) and (n1 + N1 j) ^ s = (n1 ^ s) + N1 j for s < 8
         const float2* cb = Tt + kx * rs + (n1 ^ (g & 7));
 #pragma unroll
-        for (int j = 0; j < N2; ++j) v[j] = (j < NZ && j < jmax) ? cb[N1 * j] : make_float2(0.f, 0.f);
+        for (int j = 0; j < N2; ++j)
+          v[j] = (j < NZ && (kPadded || j < jmax)) ? cb[N1 * j] : make_float2(0.f, 0.f);
       } else {
 #pragma unroll
         for (int j = 0; j < N2; ++j) {
           const int jw = n1 + N1 * j;
-          v[j] = (j < NZ && jw < R) ? Tt[kx * rs + (jw ^ (kx & 7))] : make_float2(0.f, 0.f);
+          v[j] = (j < NZ && (kPadded || jw < R)) ? Tt[kx * rs + (jw ^ (kx & 7))]
+                                                 : make_float2(0.f, 0.f);
         }
       }
-      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, gmask);
+      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, kFull);
 #pragma unroll
       for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
       if (pix_owner && r == pr) {
 #pragma unroll
         for (int q = 0; q < N2; ++q)
           if (q == pslot) pixs[0] = cmul(v[q], pph);
+      }
+    }
+    // ---- next frame's E' (the row pass has finished reading Es) ----
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
+      eprev[i] = ecur[i];
+      if (more && a < Na) {
+        ecur[i] = unpack_volt(A, nxt[i], vs);
+        Es[a] = cmul(ecur[i], gnx[i]);
       }
     }
     __syncthreads();
@@ -321,7 +359,7 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   __syncthreads();                                     // Es and pixs are reused by the next unit
 }
 
-template <int N, int MAXA>
+template <int N, int MAXA, bool TS>
 __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS;
@@ -332,6 +370,8 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
   float2* tw = Z + GROUPS * G::ZG;                     // [N2][N1] twiddles
   float2* pixs = tw + N;                               // calibrator pixel
   float2* Es = pixs + 2;                               // [Na] gain-corrected voltages
+  int* sgofs = reinterpret_cast<int*>(Es + A.n_ant);   // [rows_alloc * N1] (TS)
+  uint2* sgent = reinterpret_cast<uint2*>(sgofs + ((A.rows_alloc * N1 + 1) & ~1));  // [gmax]
 
   const int tid = threadIdx.x;
   float2* zg = Z + (tid / N1) * G::ZG;
@@ -350,11 +390,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
     const int4 wn = __ldg(A.win4 + c);
     const int span = wn.y > wn.w ? wn.y : wn.w;          // occupied rows / columns
     if (span <= N1 * (N2 / 4))
-      fused_unit<N, MAXA, N2 / 4>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
+      fused_unit<N, MAXA, N2 / 4, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
     else if (span <= N1 * (N2 / 2))
-      fused_unit<N, MAXA, N2 / 2>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
+      fused_unit<N, MAXA, N2 / 2, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
     else
-      fused_unit<N, MAXA, N2>(A, c, t0, t1, Tt, zg, tw, pixs, Es);
+      fused_unit<N, MAXA, N2, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
   }
 }
 
@@ -656,11 +696,14 @@ __global__ void unpack_ci4_kernel(const unsigned char* __restrict__ in, float2* 
 
 template <int N, int MAXA>
 cudaError_t prepare_nm(size_t smem, int* ctas) {
-  cudaError_t e = cudaFuncSetAttribute(epic_image_fused<N, MAXA>,
+  cudaError_t e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, epic_image_fused<N, MAXA>,
+  e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, epic_image_fused<N, MAXA, true>,
                                                        Cfg<N>::BT, smem);
 }
 
@@ -673,10 +716,17 @@ cudaError_t prepare_n(size_t smem, int n_ant, int* ctas) {
 
 template <int N>
 cudaError_t launch_n(const ImageArgs& a, cudaStream_t s) {
-  if (a.n_ant <= Cfg<N>::BT)
-    epic_image_fused<N, 1><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
-  else
-    epic_image_fused<N, kMaxAntPerThread><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  if (a.n_ant <= Cfg<N>::BT) {
+    if (a.gsmem)
+      epic_image_fused<N, 1, true><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+    else
+      epic_image_fused<N, 1, false><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  } else {
+    if (a.gsmem)
+      epic_image_fused<N, kMaxAntPerThread, true><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+    else
+      epic_image_fused<N, kMaxAntPerThread, false><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -769,6 +819,12 @@ size_t adjoint_smem_bytes(int n, int rows_alloc, int rs) {
   return elems * sizeof(float2);
 }
 
+int image_fused_rows(int n, int span) {
+  if (span <= n / 4) return n / 4;
+  if (span <= n / 2) return n / 2;
+  return span;
+}
+
 int image_rs_fused(int rows_alloc) {
   int rs = ((rows_alloc + 7) / 8) * 8;     // room for the (row ^ (kx & 7)) swizzle
   while (rs % 16 != 8) rs += 8;
@@ -788,6 +844,11 @@ size_t image_smem_bytes(int n, int n_ant, int rs) {
   const size_t elems = static_cast<size_t>(n) * rs + static_cast<size_t>(groups) * zg + n + 2 +
                        static_cast<size_t>(n_ant);
   return elems * sizeof(float2);
+}
+
+size_t image_table_bytes(int rows_alloc, int n1, long long gmax) {
+  return static_cast<size_t>((rows_alloc * n1 + 1) & ~1) * sizeof(int) +
+         static_cast<size_t>(gmax) * sizeof(uint2);
 }
 
 int image_fft_lanes(int n) {
@@ -811,6 +872,7 @@ cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas) {
 }
 
 cudaError_t launch_image(int n, const ImageArgs& a, cudaStream_t s) {
+  if (a.piped) return launch_piped(n, a, s);
   switch (n) {
     case 16: return launch_n<16>(a, s);
     case 32: return launch_n<32>(a, s);

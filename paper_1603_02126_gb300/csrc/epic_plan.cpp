@@ -90,6 +90,9 @@ struct epic_plan_s {
   DevBuf<int> d_cellf;          // [C][Na] fused-kernel window cell of tap (0,0)
   DevBuf<int> d_gofs;           // [C][rows_alloc][N1] fused gather: first entry per FFT lane
   DevBuf<uint2> d_gent;         // fused gather entries (antenna << 5 | j, weight bits)
+  DevBuf<int> d_gbase;          // [C + 1] first gather entry of each channel
+  int gsmem = 0;                // fused gather table held in shared memory
+  bool piped = false;           // fused path in its warp-specialised form
   DevBuf<float2> d_pixph;       // [C] calibrator-pixel phase in window coordinates
   std::vector<int> x0, cols;    // [C] first occupied column, occupied columns
   int rs_fused = 0;
@@ -188,6 +191,10 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.cellf = p->d_cellf.p;
   a.gofs = p->d_gofs.p;
   a.gent = p->d_gent.p;
+  a.gbase = p->d_gbase.p;
+  a.gsmem = p->gsmem;
+  a.piped = p->piped ? 1 : 0;
+  a.err = p->d_err.p;
   a.wts = p->d_wts.p;
   a.wgain = p->d_wgain.p;
   a.vscale = p->d_vscale.p;
@@ -446,7 +453,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     return fail(EPIC_ERR_INVALID_ARG, "unknown input format");
   if (d->precision != EPIC_PREC_FP32 && d->precision != EPIC_PREC_FP16 && d->precision != EPIC_PREC_BF16)
     return fail(EPIC_ERR_INVALID_ARG, "unknown precision");
-  if (d->precision != EPIC_PREC_FP32 && d->path == EPIC_PATH_FUSED)
+  if (d->precision != EPIC_PREC_FP32 && (d->path == EPIC_PATH_FUSED || d->path == EPIC_PATH_PIPED))
     return fail(EPIC_ERR_UNSUPPORTED, "FP16/BF16 run on the tensor-core column DFT (not the fused path)");
   for (int c = 0; c < d->n_chan; ++c)
     if (!(d->freq_hz[c] > 0) || !std::isfinite(d->freq_hz[c]))
@@ -455,7 +462,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     if (!std::isfinite(d->ant_xy_m[i])) return fail(EPIC_ERR_INVALID_ARG, "non-finite antenna position");
 
   if (d->path != EPIC_PATH_AUTO && d->path != EPIC_PATH_FUSED && d->path != EPIC_PATH_UNFUSED &&
-      d->path != EPIC_PATH_CLUSTER)
+      d->path != EPIC_PATH_CLUSTER && d->path != EPIC_PATH_PIPED)
     return fail(EPIC_ERR_INVALID_ARG, "unknown path");
   if (d->path == EPIC_PATH_CLUSTER &&
       (!epic::cluster_supported(d->grid_n) || d->n_ant > 256 * epic::cluster_size(d->grid_n) ||
@@ -464,7 +471,9 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   epic::ImageKernelShape shape{};
   const bool fused_shape = epic::image_kernel_shape(d->grid_n, &shape) && d->n_ant <= shape.max_ant;
   const bool unfused_ok = epic::unfused_supported(d->grid_n);
-  if (d->path == EPIC_PATH_FUSED && !fused_shape)
+  if (d->path == EPIC_PATH_PIPED && !epic::piped_supported(d->grid_n, d->n_ant))
+    return fail(EPIC_ERR_UNSUPPORTED, "warp-specialised fused path: grid_n 64 or 128, n_ant <= 512");
+  if ((d->path == EPIC_PATH_FUSED || d->path == EPIC_PATH_PIPED) && !fused_shape)
     return fail(EPIC_ERR_UNSUPPORTED, "fused path: grid_n must be 16..128 and n_ant <= " +
                                           std::to_string(shape.max_ant > 0 ? shape.max_ant : 2048));
   if (d->path == EPIC_PATH_UNFUSED && !unfused_ok)
@@ -615,8 +624,42 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
   }
   p->rs_fused = epic::image_rs_fused(p->rows_alloc);
-  if (fused) {
+  if (fused && d->path == EPIC_PATH_PIPED && epic::piped_supported(N, Na)) {
+    // warp-specialised form: two spectra slots; gather table in shared
+    // memory when it fits (entries per channel <= Na K^2 + one per FFT lane)
+    const long long gmax = static_cast<long long>(Na) * KK +
+                           static_cast<long long>(p->rows_alloc) * epic::image_fft_lanes(N);
+    const size_t s1 = epic::piped_smem_bytes(N, Na, p->rs_fused, p->rows_alloc, gmax);
+    const size_t s0 = epic::piped_smem_bytes(N, Na, p->rs_fused, p->rows_alloc, 0);
+    if (s1 <= static_cast<size_t>(smem_optin)) {
+      p->piped = true;
+      p->smem = s1;
+      p->gsmem = 1;
+    } else if (s0 <= static_cast<size_t>(smem_optin)) {
+      p->piped = true;
+      p->smem = s0;
+      p->gsmem = 0;
+    }
+  }
+  if (d->path == EPIC_PATH_PIPED && !p->piped) {
+    delete p;
+    return fail(EPIC_ERR_UNSUPPORTED, "warp-specialised fused path: array footprint exceeds shared memory");
+  }
+  if (fused && !p->piped) {
+    int zrows = p->rows_alloc;
+    for (int c = 0; c < C; ++c)
+      zrows = std::max(zrows, epic::image_fused_rows(N, std::max(p->rows[c], p->cols[c])));
+    p->rs_fused = epic::image_rs_fused(zrows);
     p->smem = epic::image_smem_bytes(N, Na, p->rs_fused);
+    // the gather table stays in shared memory when it fits (entries per
+    // channel <= Na K^2 taps + one sentinel per FFT lane)
+    const int n1 = epic::image_fft_lanes(N);
+    const long long gmax = static_cast<long long>(Na) * KK + static_cast<long long>(p->rows_alloc) * n1;
+    const size_t with_tab = p->smem + epic::image_table_bytes(p->rows_alloc, n1, gmax);
+    if (with_tab <= static_cast<size_t>(smem_optin)) {
+      p->smem = with_tab;
+      p->gsmem = 1;
+    }
     if (p->smem > static_cast<size_t>(smem_optin)) {
       const std::string msg = "array footprint needs " + std::to_string(p->smem) +
                               " B of shared memory in the fused kernel (limit " +
@@ -659,7 +702,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     // tables built below with the device tables
   } else if (fused) {
     int per_sm = 0;
-    e = epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
+    e = p->piped ? epic::piped_prepare(N, p->smem, p->gsmem != 0, &per_sm)
+                 : epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
       delete p;
       return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
@@ -693,14 +737,16 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
   // fused path: per FFT lane (window row r, lane n1 = x mod N1) the taps on
   // its columns x = n1 + N1 j, sorted by j, then a sentinel entry (j = 31)
-  std::vector<int> gofs;
+  std::vector<int> gofs, gbase;
   std::vector<uint2> gent;
   if (p->path == EPIC_PATH_FUSED) {
     const int N1 = epic::image_fft_lanes(N);
     const int RA = p->rows_alloc;
     gofs.assign(static_cast<size_t>(C) * RA * N1, 0);
     std::vector<std::vector<std::pair<unsigned, float>>> lists(static_cast<size_t>(RA) * N1);
+    gbase.assign(static_cast<size_t>(C) + 1, 0);
     for (int c = 0; c < C; ++c) {
+      gbase[c] = static_cast<int>(gent.size());
       for (auto& l : lists) l.clear();
       for (int a = 0; a < Na; ++a) {
         if (p->flags[a]) continue;
@@ -722,7 +768,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                                                 const std::pair<unsigned, float>& v) {
           return (u.first & 31u) < (v.first & 31u);
         });
-        gofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(gent.size());
+        gofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(gent.size()) - gbase[c];
         for (const auto& en : l) {
           uint2 q;
           q.x = en.first;
@@ -732,6 +778,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
         gent.push_back(make_uint2(31u, 0u));
       }
     }
+    gbase[C] = static_cast<int>(gent.size());
   }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
   // cluster path: stencil (top row, first column) in window coordinates,
@@ -780,7 +827,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                       up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
                       up(p->d_cellf, cellf), up(p->d_pixph, pixph), up(p->d_rowcol, rowcol),
                       up(p->d_order, order), up(p->d_ranges, ranges), up(p->d_gofs, gofs),
-                      up(p->d_gent, gent)};
+                      up(p->d_gent, gent), up(p->d_gbase, gbase)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -812,6 +859,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_cellf.release();
   p->d_gofs.release();
   p->d_gent.release();
+  p->d_gbase.release();
   p->d_pixph.release();
   p->d_rowcol.release();
   p->d_order.release();
@@ -860,7 +908,7 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info) {
   info->smem_bytes = p->smem;
   info->frames_pending = p->frames;
   info->iteration = p->iteration;
-  info->path = p->path;
+  info->path = p->piped ? EPIC_PATH_PIPED : p->path;
   info->batch_time = p->ws_time;
   return EPIC_OK;
 }
