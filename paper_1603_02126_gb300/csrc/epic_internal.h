@@ -29,6 +29,7 @@ struct ImageArgs {
   const int* gbase;        // [C + 1] first entry of each channel in gent
   int gsmem;               // 1: the channel's table is copied to shared memory per unit
   int piped;               // 1: warp-specialised form (epic_image_piped)
+  int steps;               // fused form: frames per step (spectra slots), 1 or 2
   int* err;                // device flag: a bounded wait timed out (piped form)
   const float2* pixph;     // [C] (-1)^(k0x+k0y) e^{2 pi i (x0 k0x + y0 k0y)/N}
   const float2* twid;      // [N] e^{+2 pi i m / N}
@@ -56,22 +57,22 @@ struct ImageKernelShape {
 bool image_kernel_shape(int n, ImageKernelShape* out);
 int image_rs(int rows_alloc);
 int image_rs_fused(int rows_alloc);
-// Spectra rows the fused kernel's column pass reads for an occupied window
-// of `span` rows / columns: N/4 or N/2 (zero-padded pruned forms), else span.
-int image_fused_rows(int n, int span);
+
 // Dynamic shared memory of the adjoint kernel (layout: window [rows][N],
 // spectra [N][rs], FFT exchange, twiddles).
 size_t adjoint_smem_bytes(int n, int rows_alloc, int rs);
 // Row stride of the fused kernel's grid window, N + N1.
 int image_window_stride(int n);
-size_t image_smem_bytes(int n, int n_ant, int rs);
+size_t image_smem_bytes(int n, int n_ant, int rs, int steps);
+// Frames per step the fused kernel supports for grid side n (1 or 2).
+int image_max_steps(int n);
 // Shared memory of a channel's gather table (lane offsets + up to gmax entries).
 size_t image_table_bytes(int rows_alloc, int n1, long long gmax);
 // Lanes per 1-D FFT (N1) of the fused kernel: window column x is entry
 // block j = x / N1 of lane x % N1.
 int image_fft_lanes(int n);
 // Opt in to the shared memory and report resident CTAs per SM.
-cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas_per_sm);
+cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int steps, int* ctas_per_sm);
 cudaError_t launch_image(int n, const ImageArgs& a, cudaStream_t s);
 
 // Warp-specialised fused form (N = 64, 128): producer warps grid and row-FFT

@@ -131,8 +131,12 @@ __device__ __forceinline__ float2 unpack_volt(const ImageArgs& A, const RawVolt&
 // sorted by j and closed by a sentinel (j = 31).  Each frame the lane sums
 // w * E'_a over its list straight into its FFT inputs; E'_a = E_a / g_a
 // (Eq. 8) sits in shared memory, computed once per antenna while the
-// previous frame's column FFTs run.  No atomics, and the sum order is fixed.
-template <int N, int MAXA, int NZ, bool TS>
+// previous step's column FFTs run.  No atomics, and the sum order is fixed.
+//
+// The unit advances F frames per step (F spectra slots): one row pass for
+// the rows of all F frames, a CTA barrier, one column pass over all F
+// frames, a barrier.  More work between barriers keeps more warps busy.
+template <int N, int MAXA, int NZ, bool TS, int F>
 __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long t0, long long t1,
                                            float2* Tt, float2* zg, const float2* tw, float2* pixs,
                                            float2* Es, int* sgofs, uint2* sgent) {
@@ -142,9 +146,9 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   const int g = tid / N1;
   const int n1 = tid % N1;
   constexpr int kGroupsPerWarp = 32 / N1;
-  constexpr bool kPadded = NZ < N2;                    // spectra rows padded to N1 * NZ
   const int Na = A.n_ant;
   const int rs = A.rs;
+  const size_t tslot = static_cast<size_t>(N) * rs;   // one frame's spectra
 
   const int4 wn = __ldg(A.win4 + c);                   // (y0, rows, x0, cols)
   const int R = wn.y;
@@ -169,58 +173,75 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   const bool pix_owner = A.do_cal && g == pg && n1 == pn1;
   const float2 pph = A.do_cal ? __ldg(A.pixph + c) : make_float2(1.f, 0.f);
 
-  // spectra buffer cleared: rows R .. N1 NZ - 1 are read by the column pass
-  for (int i = tid; i < N * rs; i += BT) Tt[i] = make_float2(0.f, 0.f);
-
   float acc[G::NACC];
 #pragma unroll
   for (int i = 0; i < G::NACC; ++i) acc[i] = 0.f;
-  float2 kac[MAXA], ecur[MAXA], eprev[MAXA];
+  // raw voltages (scaled) of the current and previous step, for Eqs. 12, 15
+  float2 kac[MAXA], ecur[F][MAXA], eprev[F][MAXA];
   float pac[MAXA];
 #pragma unroll
   for (int i = 0; i < MAXA; ++i) {
     kac[i] = make_float2(0.f, 0.f);
-    eprev[i] = make_float2(0.f, 0.f);
     pac[i] = 0.f;
-    // frame t0: raw voltages (for the correlation) and E' = E / g
-    const int a = tid + BT * i;
-    ecur[i] = make_float2(0.f, 0.f);
-    if (a < Na) {
-      ecur[i] = unpack_volt(A, fetch_volt(A, t0, c, a), vs);
-      Es[a] = cmul(ecur[i], __ldg(wg + a));
-    }
   }
-  __syncthreads();
-
-  for (long long t = t0; t < t1; ++t) {
-    const bool more = t + 1 < t1;
-    // next frame's voltages: pulled into L1 now (no register waits on
-    // them), loaded after the row pass
-    if (more) {
-      const size_t esz = A.input_fmt == 0 ? 1 : sizeof(float2);
-      const size_t off = (static_cast<size_t>(t + 1) * A.n_chan + c) * Na * esz;
-      const uintptr_t lo = (reinterpret_cast<uintptr_t>(A.volt) + off) & ~static_cast<uintptr_t>(127);
-      const uintptr_t hi = reinterpret_cast<uintptr_t>(A.volt) + off + Na * esz;
-      for (uintptr_t q = lo + static_cast<uintptr_t>(tid) * 128; q < hi; q += BT * 128)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
-    }
-
-    // ---- B: correlation of the previous frame, then gather + row FFTs ----
-    if (A.do_cal && t > t0) {
-      const float2 p = pixs[0];
+  // first step: raw voltages and E' = E / g
 #pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        const float2 e = eprev[i];
-        kac[i].x += e.x * p.x + e.y * p.y;
-        kac[i].y += e.y * p.x - e.x * p.y;
-        pac[i] += e.x * e.x + e.y * e.y;
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
+      eprev[f][i] = make_float2(0.f, 0.f);
+      ecur[f][i] = make_float2(0.f, 0.f);
+      if (a < Na && t0 + f < t1) {
+        ecur[f][i] = unpack_volt(A, fetch_volt(A, t0 + f, c, a), vs);
+        Es[f * Na + a] = cmul(ecur[f][i], __ldg(wg + a));
       }
     }
-    // whole warps step through the rows together (full-warp syncs in the
-    // FFT exchange); lanes past the last row transform zeros and store nothing
-    for (int rb = g - g % kGroupsPerWarp; rb < R; rb += GROUPS) {
-      const int row = rb + g % kGroupsPerWarp;
-      const bool live = row < R;
+  __syncthreads();
+
+  int nprev = 0;                                       // frames of the previous step
+  for (long long t = t0; t < t1; t += F) {
+    const int nf = static_cast<int>(t1 - t < F ? t1 - t : F);
+    const long long tn = t + F;                        // next step's first frame
+    const int nfn = static_cast<int>(t1 - tn <= 0 ? 0 : (t1 - tn < F ? t1 - tn : F));
+    // next step's voltages: pulled into L1 now, loaded after the row pass
+    {
+      const size_t esz = A.input_fmt == 0 ? 1 : sizeof(float2);
+      for (int f = 0; f < nfn; ++f) {
+        const size_t off = (static_cast<size_t>(tn + f) * A.n_chan + c) * Na * esz;
+        const uintptr_t lo = (reinterpret_cast<uintptr_t>(A.volt) + off) & ~static_cast<uintptr_t>(127);
+        const uintptr_t hi = reinterpret_cast<uintptr_t>(A.volt) + off + Na * esz;
+        for (uintptr_t q = lo + static_cast<uintptr_t>(tid) * 128; q < hi; q += BT * 128)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+      }
+    }
+
+    // ---- B: correlation of the previous step, then gather + row FFTs ----
+    if (A.do_cal) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        if (f < nprev) {
+          const float2 p = pixs[f];
+#pragma unroll
+          for (int i = 0; i < MAXA; ++i) {
+            const float2 e = eprev[f][i];
+            kac[i].x += e.x * p.x + e.y * p.y;
+            kac[i].y += e.y * p.x - e.x * p.y;
+            pac[i] += e.x * e.x + e.y * e.y;
+          }
+        }
+      }
+    }
+    // row tasks (frame, row) of the step; whole warps step through them
+    // together (full-warp syncs in the FFT exchange); lanes past the last
+    // task transform zeros and store nothing
+    const int ntask = nf * R;
+    for (int rb = g - g % kGroupsPerWarp; rb < ntask; rb += GROUPS) {
+      const int task = rb + g % kGroupsPerWarp;
+      const bool live = task < ntask;
+      const int f = (F > 1 && live) ? task / R : 0;
+      const int row = live ? task - f * R : 0;
+      const float2* Ef = Es + f * Na;
       float2 v[N2];
 #pragma unroll
       for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
@@ -231,7 +252,7 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
         for (int j = 0; j < NZ; ++j) {
           float2 sum = make_float2(0.f, 0.f);
           while ((en.x & 31u) == static_cast<unsigned>(j)) {
-            const float2 x = Es[en.x >> 5];
+            const float2 x = Ef[en.x >> 5];
             const float w = __uint_as_float(en.y);
             sum.x = fmaf(w, x.x, sum.x);
             sum.y = fmaf(w, x.y, sum.y);
@@ -243,9 +264,10 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
       }
       fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, kFull);
       if (live) {
+        float2* Tf = Tt + f * tslot;
         if constexpr (N1 % 8 == 0) {
           // kx = n1 + N1 h + N2 k1 = n1 (mod 8): one swizzled row index per thread
-          float2* tb = Tt + n1 * rs + (row ^ n1);
+          float2* tb = Tf + n1 * rs + (row ^ n1);
 #pragma unroll
           for (int h = 0; h < H; ++h)
 #pragma unroll
@@ -256,77 +278,88 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
               const int kx = n1 + N1 * h + N2 * k1;
-              Tt[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
+              Tf[kx * rs + (row ^ (kx & 7))] = v[h * N1 + k1];
             }
         }
       }
     }
     __syncthreads();
 
-    // next frame's voltages and gains, used after the column pass
-    RawVolt nxt[MAXA];
+    // next step's voltages and gains, used after the column pass
+    RawVolt nxt[F][MAXA];
     float2 gnx[MAXA];
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
       const int a = tid + BT * i;
-      const bool ld = more && a < Na;
-      nxt[i] = ld ? fetch_volt(A, t + 1, c, a) : RawVolt{0u, make_float2(0.f, 0.f)};
-      gnx[i] = ld ? __ldg(wg + a) : make_float2(0.f, 0.f);
+      gnx[i] = (nfn > 0 && a < Na) ? __ldg(wg + a) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+        nxt[f][i] = (f < nfn && a < Na) ? fetch_volt(A, tn + f, c, a) : RawVolt{0u, make_float2(0.f, 0.f)};
     }
 
     // ---- C: column FFTs, |E|^2 accumulation, calibrator pixel ----
-    // (pruned forms: spectra rows R .. N1 NZ - 1 hold zeros, so the loads
-    // need no bounds test; the full form reads rows < R only)
     const int jmax = (R - n1 + N1 - 1) / N1;             // this lane's rows n1 + N1 j < R
 #pragma unroll
-    for (int r = 0; r < G::COLROUNDS; ++r) {
-      const int kx = g + GROUPS * r;
-      float2 v[N2];
-      if constexpr (N1 % 8 == 0) {
-        // kx = g (mod 8) and (n1 + N1 j) ^ s = (n1 ^ s) + N1 j for s < 8
-        const float2* cb = Tt + kx * rs + (n1 ^ (g & 7));
+    for (int f = 0; f < F; ++f) {
+      if (f < nf) {
+        const float2* Tf = Tt + f * tslot;
 #pragma unroll
-        for (int j = 0; j < N2; ++j)
-          v[j] = (j < NZ && (kPadded || j < jmax)) ? cb[N1 * j] : make_float2(0.f, 0.f);
-      } else {
+        for (int r = 0; r < G::COLROUNDS; ++r) {
+          const int kx = g + GROUPS * r;
+          float2 v[N2];
+          if constexpr (N1 % 8 == 0) {
+            // kx = g (mod 8) and (n1 + N1 j) ^ s = (n1 ^ s) + N1 j for s < 8
+            const float2* cb = Tf + kx * rs + (n1 ^ (g & 7));
 #pragma unroll
-        for (int j = 0; j < N2; ++j) {
-          const int jw = n1 + N1 * j;
-          v[j] = (j < NZ && (kPadded || jw < R)) ? Tt[kx * rs + (jw ^ (kx & 7))]
-                                                 : make_float2(0.f, 0.f);
+            for (int j = 0; j < N2; ++j) v[j] = (j < NZ && j < jmax) ? cb[N1 * j] : make_float2(0.f, 0.f);
+          } else {
+#pragma unroll
+            for (int j = 0; j < N2; ++j) {
+              const int jw = n1 + N1 * j;
+              v[j] = (j < NZ && jw < R) ? Tf[kx * rs + (jw ^ (kx & 7))] : make_float2(0.f, 0.f);
+            }
+          }
+          fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, kFull);
+#pragma unroll
+          for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
+          if (pix_owner && r == pr) {
+#pragma unroll
+            for (int q = 0; q < N2; ++q)
+              if (q == pslot) pixs[f] = cmul(v[q], pph);
+          }
         }
       }
-      fft::fft_lanes_p<N1, N2, NZ>(v, n1, zg, tw, kFull);
-#pragma unroll
-      for (int q = 0; q < N2; ++q) acc[r * N2 + q] += v[q].x * v[q].x + v[q].y * v[q].y;
-      if (pix_owner && r == pr) {
-#pragma unroll
-        for (int q = 0; q < N2; ++q)
-          if (q == pslot) pixs[0] = cmul(v[q], pph);
-      }
     }
-    // ---- next frame's E' (the row pass has finished reading Es) ----
+    // ---- next step's E' (the row pass has finished reading Es) ----
 #pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      const int a = tid + BT * i;
-      eprev[i] = ecur[i];
-      if (more && a < Na) {
-        ecur[i] = unpack_volt(A, nxt[i], vs);
-        Es[a] = cmul(ecur[i], gnx[i]);
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int i = 0; i < MAXA; ++i) {
+        const int a = tid + BT * i;
+        eprev[f][i] = ecur[f][i];
+        if (f < nfn && a < Na) {
+          ecur[f][i] = unpack_volt(A, nxt[f][i], vs);
+          Es[f * Na + a] = cmul(ecur[f][i], gnx[i]);
+        }
       }
-    }
+    nprev = nf;
     __syncthreads();
   }
 
-  // correlation of the unit's last frame
+  // correlation of the unit's last step
   if (A.do_cal) {
-    const float2 p = pixs[0];
 #pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      const float2 e = ecur[i];
-      kac[i].x += e.x * p.x + e.y * p.y;
-      kac[i].y += e.y * p.x - e.x * p.y;
-      pac[i] += e.x * e.x + e.y * e.y;
+    for (int f = 0; f < F; ++f) {
+      if (f < nprev) {
+        const float2 p = pixs[f];
+#pragma unroll
+        for (int i = 0; i < MAXA; ++i) {
+          const float2 e = eprev[f][i];
+          kac[i].x += e.x * p.x + e.y * p.y;
+          kac[i].y += e.y * p.x - e.x * p.y;
+          pac[i] += e.x * e.x + e.y * e.y;
+        }
+      }
     }
   }
 
@@ -359,18 +392,18 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   __syncthreads();                                     // Es and pixs are reused by the next unit
 }
 
-template <int N, int MAXA, bool TS>
+template <int N, int MAXA, bool TS, int F>
 __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArgs A) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Tt = reinterpret_cast<float2*>(smem_raw);   // [N][rs] row spectra, transposed, swizzled
-  float2* Z = Tt + N * A.rs;                           // [GROUPS][ZG] FFT exchange
+  float2* Tt = reinterpret_cast<float2*>(smem_raw);   // [F][N][rs] row spectra, transposed, swizzled
+  float2* Z = Tt + F * N * A.rs;                       // [GROUPS][ZG] FFT exchange
   float2* tw = Z + GROUPS * G::ZG;                     // [N2][N1] twiddles
-  float2* pixs = tw + N;                               // calibrator pixel
-  float2* Es = pixs + 2;                               // [Na] gain-corrected voltages
-  int* sgofs = reinterpret_cast<int*>(Es + A.n_ant);   // [rows_alloc * N1] (TS)
+  float2* pixs = tw + N;                               // [4] calibrator pixels of the step
+  float2* Es = pixs + 4;                               // [F][Na] gain-corrected voltages
+  int* sgofs = reinterpret_cast<int*>(Es + F * A.n_ant);  // [rows_alloc * N1] (TS)
   uint2* sgent = reinterpret_cast<uint2*>(sgofs + ((A.rows_alloc * N1 + 1) & ~1));  // [gmax]
 
   const int tid = threadIdx.x;
@@ -390,11 +423,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
     const int4 wn = __ldg(A.win4 + c);
     const int span = wn.y > wn.w ? wn.y : wn.w;          // occupied rows / columns
     if (span <= N1 * (N2 / 4))
-      fused_unit<N, MAXA, N2 / 4, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2 / 4, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
     else if (span <= N1 * (N2 / 2))
-      fused_unit<N, MAXA, N2 / 2, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2 / 2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
     else
-      fused_unit<N, MAXA, N2, TS>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
   }
 }
 
@@ -694,38 +727,51 @@ __global__ void unpack_ci4_kernel(const unsigned char* __restrict__ in, float2* 
   }
 }
 
-template <int N, int MAXA>
-cudaError_t prepare_nm(size_t smem, int* ctas) {
-  cudaError_t e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, true>,
+template <int N, int MAXA, int F>
+cudaError_t prepare_nmf(size_t smem, int* ctas) {
+  cudaError_t e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, true, F>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, false>,
+  e = cudaFuncSetAttribute(epic_image_fused<N, MAXA, false, F>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, epic_image_fused<N, MAXA, true>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, epic_image_fused<N, MAXA, true, F>,
                                                        Cfg<N>::BT, smem);
 }
 
+// Frames per step: 2 for the 512-thread shapes (N = 64, 128), else 1.
+template <int N>
+constexpr int kMaxSteps = Cfg<N>::BT >= 512 ? 2 : 1;
+
 // One antenna per thread when Na <= CTA size, else up to kMaxAntPerThread.
 template <int N>
-cudaError_t prepare_n(size_t smem, int n_ant, int* ctas) {
-  if (n_ant <= Cfg<N>::BT) return prepare_nm<N, 1>(smem, ctas);
-  return prepare_nm<N, kMaxAntPerThread>(smem, ctas);
+cudaError_t prepare_n(size_t smem, int n_ant, int steps, int* ctas) {
+  if (steps == 2 && kMaxSteps<N> == 2) {
+    if (n_ant <= Cfg<N>::BT) return prepare_nmf<N, 1, kMaxSteps<N>>(smem, ctas);
+    return prepare_nmf<N, kMaxAntPerThread, kMaxSteps<N>>(smem, ctas);
+  }
+  if (n_ant <= Cfg<N>::BT) return prepare_nmf<N, 1, 1>(smem, ctas);
+  return prepare_nmf<N, kMaxAntPerThread, 1>(smem, ctas);
+}
+
+template <int N, int MAXA, int F>
+void launch_nmf(const ImageArgs& a, cudaStream_t s) {
+  if (a.gsmem)
+    epic_image_fused<N, MAXA, true, F><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+  else
+    epic_image_fused<N, MAXA, false, F><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
 }
 
 template <int N>
 cudaError_t launch_n(const ImageArgs& a, cudaStream_t s) {
+  const bool two = a.steps == 2 && kMaxSteps<N> == 2;
   if (a.n_ant <= Cfg<N>::BT) {
-    if (a.gsmem)
-      epic_image_fused<N, 1, true><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
-    else
-      epic_image_fused<N, 1, false><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+    if (two) launch_nmf<N, 1, kMaxSteps<N>>(a, s);
+    else launch_nmf<N, 1, 1>(a, s);
   } else {
-    if (a.gsmem)
-      epic_image_fused<N, kMaxAntPerThread, true><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
-    else
-      epic_image_fused<N, kMaxAntPerThread, false><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
+    if (two) launch_nmf<N, kMaxAntPerThread, kMaxSteps<N>>(a, s);
+    else launch_nmf<N, kMaxAntPerThread, 1>(a, s);
   }
   return cudaGetLastError();
 }
@@ -819,19 +865,13 @@ size_t adjoint_smem_bytes(int n, int rows_alloc, int rs) {
   return elems * sizeof(float2);
 }
 
-int image_fused_rows(int n, int span) {
-  if (span <= n / 4) return n / 4;
-  if (span <= n / 2) return n / 2;
-  return span;
-}
-
 int image_rs_fused(int rows_alloc) {
   int rs = ((rows_alloc + 7) / 8) * 8;     // room for the (row ^ (kx & 7)) swizzle
   while (rs % 16 != 8) rs += 8;
   return rs;
 }
 
-size_t image_smem_bytes(int n, int n_ant, int rs) {
+size_t image_smem_bytes(int n, int n_ant, int rs, int steps) {
   int groups = 0, zg = 0;
   switch (n) {
     case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
@@ -840,9 +880,9 @@ size_t image_smem_bytes(int n, int n_ant, int rs) {
     case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
     default: return 0;
   }
-  // spectra [N][rs], exchange, twiddles, calibrator pixel, E' [Na]
-  const size_t elems = static_cast<size_t>(n) * rs + static_cast<size_t>(groups) * zg + n + 2 +
-                       static_cast<size_t>(n_ant);
+  // spectra [F][N][rs], exchange, twiddles, calibrator pixels, E' [F][Na]
+  const size_t elems = static_cast<size_t>(steps) * n * rs + static_cast<size_t>(groups) * zg + n + 4 +
+                       static_cast<size_t>(steps) * n_ant;
   return elems * sizeof(float2);
 }
 
@@ -861,12 +901,22 @@ int image_fft_lanes(int n) {
   }
 }
 
-cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int* ctas) {
+int image_max_steps(int n) {
   switch (n) {
-    case 16: return prepare_n<16>(smem, n_ant, ctas);
-    case 32: return prepare_n<32>(smem, n_ant, ctas);
-    case 64: return prepare_n<64>(smem, n_ant, ctas);
-    case 128: return prepare_n<128>(smem, n_ant, ctas);
+    case 16: return kMaxSteps<16>;
+    case 32: return kMaxSteps<32>;
+    case 64: return kMaxSteps<64>;
+    case 128: return kMaxSteps<128>;
+    default: return 1;
+  }
+}
+
+cudaError_t image_kernel_prepare(int n, size_t smem, int n_ant, int steps, int* ctas) {
+  switch (n) {
+    case 16: return prepare_n<16>(smem, n_ant, steps, ctas);
+    case 32: return prepare_n<32>(smem, n_ant, steps, ctas);
+    case 64: return prepare_n<64>(smem, n_ant, steps, ctas);
+    case 128: return prepare_n<128>(smem, n_ant, steps, ctas);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -93,6 +93,7 @@ struct epic_plan_s {
   DevBuf<int> d_gbase;          // [C + 1] first gather entry of each channel
   int gsmem = 0;                // fused gather table held in shared memory
   bool piped = false;           // fused path in its warp-specialised form
+  int steps = 1;                // fused form: frames per step
   DevBuf<float2> d_pixph;       // [C] calibrator-pixel phase in window coordinates
   std::vector<int> x0, cols;    // [C] first occupied column, occupied columns
   int rs_fused = 0;
@@ -194,6 +195,7 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.gbase = p->d_gbase.p;
   a.gsmem = p->gsmem;
   a.piped = p->piped ? 1 : 0;
+  a.steps = p->steps;
   a.err = p->d_err.p;
   a.wts = p->d_wts.p;
   a.wgain = p->d_wgain.p;
@@ -646,22 +648,26 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     return fail(EPIC_ERR_UNSUPPORTED, "warp-specialised fused path: array footprint exceeds shared memory");
   }
   if (fused && !p->piped) {
-    int zrows = p->rows_alloc;
-    for (int c = 0; c < C; ++c)
-      zrows = std::max(zrows, epic::image_fused_rows(N, std::max(p->rows[c], p->cols[c])));
-    p->rs_fused = epic::image_rs_fused(zrows);
-    p->smem = epic::image_smem_bytes(N, Na, p->rs_fused);
-    // the gather table stays in shared memory when it fits (entries per
-    // channel <= Na K^2 taps + one sentinel per FFT lane)
+    // shape preference: two frames per step, then one; the gather table in
+    // shared memory when it fits (entries per channel <= Na K^2 taps + one
+    // sentinel per FFT lane), else read through L1
     const int n1 = epic::image_fft_lanes(N);
     const long long gmax = static_cast<long long>(Na) * KK + static_cast<long long>(p->rows_alloc) * n1;
-    const size_t with_tab = p->smem + epic::image_table_bytes(p->rows_alloc, n1, gmax);
-    if (with_tab <= static_cast<size_t>(smem_optin)) {
-      p->smem = with_tab;
-      p->gsmem = 1;
-    }
-    if (p->smem > static_cast<size_t>(smem_optin)) {
-      const std::string msg = "array footprint needs " + std::to_string(p->smem) +
+    const size_t tab = epic::image_table_bytes(p->rows_alloc, n1, gmax);
+    bool placed = false;
+    for (int steps = epic::image_max_steps(N); steps >= 1 && !placed; --steps)
+      for (int ts = 1; ts >= 0 && !placed; --ts) {
+        const size_t need = epic::image_smem_bytes(N, Na, p->rs_fused, steps) + (ts ? tab : 0);
+        if (need <= static_cast<size_t>(smem_optin)) {
+          p->smem = need;
+          p->gsmem = ts;
+          p->steps = steps;
+          placed = true;
+        }
+      }
+    if (!placed) {
+      const std::string msg = "array footprint needs " +
+                              std::to_string(epic::image_smem_bytes(N, Na, p->rs_fused, 1)) +
                               " B of shared memory in the fused kernel (limit " +
                               std::to_string(smem_optin) + ")";
       if (d->path == EPIC_PATH_FUSED || !unfused_ok) {
@@ -703,7 +709,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   } else if (fused) {
     int per_sm = 0;
     e = p->piped ? epic::piped_prepare(N, p->smem, p->gsmem != 0, &per_sm)
-                 : epic::image_kernel_prepare(N, p->smem, Na, &per_sm);
+                 : epic::image_kernel_prepare(N, p->smem, Na, p->steps, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
       delete p;
       return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
