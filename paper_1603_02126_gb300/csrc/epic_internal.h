@@ -24,8 +24,9 @@ struct ImageArgs {
   const int* cellf;        // [C][Na] window cell (row * (N + N1) + col - x0); -1 = flagged
   const int* gofs;         // [C][rows_alloc][N1] first gather entry of each FFT lane,
                            // relative to the channel's first entry
-  const uint2* gent;       // gather entries (antenna << 5 | column block j, weight bits);
-                           // each lane's list sorted by j and closed by j = 31
+  const uint4* gcnt;       // [C][rows_alloc][N1] entries of each column block j (byte j)
+  const uint2* gent;       // gather entries (antenna, weight bits), lane by lane,
+                           // grouped by column block j
   const int* gbase;        // [C + 1] first entry of each channel in gent
   int gsmem;               // 1: the channel's table is copied to shared memory per unit
   int piped;               // 1: warp-specialised form (epic_image_piped)

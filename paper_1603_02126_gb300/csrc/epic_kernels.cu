@@ -127,8 +127,9 @@ __device__ __forceinline__ float2 unpack_volt(const ImageArgs& A, const RawVolt&
 //
 // Gridding (Eq. 9) is a gather: the array layout is fixed for the plan, so
 // the host lists, for every FFT lane (window row, lane n1), the taps that
-// land on the lane's columns n1 + N1 j as entries (antenna << 5 | j, weight),
-// sorted by j and closed by a sentinel (j = 31).  Each frame the lane sums
+// land on the lane's columns n1 + N1 j as entries (antenna, weight), grouped
+// by j, with the group lengths as bytes of one 16-byte word per lane (loop
+// bounds that do not wait on the entry loads).  Each frame the lane sums
 // w * E'_a over its list straight into its FFT inputs; E'_a = E_a / g_a
 // (Eq. 8) sits in shared memory, computed once per antenna while the
 // previous step's column FFTs run.  No atomics, and the sum order is fixed.
@@ -139,7 +140,7 @@ __device__ __forceinline__ float2 unpack_volt(const ImageArgs& A, const RawVolt&
 template <int N, int MAXA, int NZ, bool TS, int F>
 __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long t0, long long t1,
                                            float2* Tt, float2* zg, const float2* tw, float2* pixs,
-                                           float2* Es, int* sgofs, uint2* sgent) {
+                                           float2* Es, int* sgofs, uint4* sgcnt, uint2* sgent) {
   using G = Geo<N>;
   constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
   const int tid = threadIdx.x;
@@ -158,11 +159,15 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
   // else read through L1
   const int gb = __ldg(A.gbase + c);
   const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
+  const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * N1;
   const uint2* gent = A.gent + gb;
   if constexpr (TS) {
     const int gn = __ldg(A.gbase + c + 1) - gb;
     for (int i = tid; i < gn; i += BT) sgent[i] = __ldg(gent + i);
-    for (int i = tid; i < R * N1; i += BT) sgofs[i] = __ldg(gofs + i);
+    for (int i = tid; i < R * N1; i += BT) {
+      sgofs[i] = __ldg(gofs + i);
+      sgcnt[i] = __ldg(gcnt + i);
+    }
   }
 
   // calibrator pixel: column round, group, lane and register slot, phase
@@ -246,19 +251,23 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
 #pragma unroll
       for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
       if (live) {
-        int e = TS ? sgofs[row * N1 + n1] : __ldg(gofs + row * N1 + n1);
-        uint2 en = TS ? sgent[e] : __ldg(gent + e);
+        const int li = row * N1 + n1;
+        int e = TS ? sgofs[li] : __ldg(gofs + li);
+        const uint4 cw = TS ? sgcnt[li] : __ldg(gcnt + li);
+        const unsigned cv[4] = {cw.x, cw.y, cw.z, cw.w};
+        const uint2* ge = TS ? sgent : gent;
 #pragma unroll
         for (int j = 0; j < NZ; ++j) {
+          const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
           float2 sum = make_float2(0.f, 0.f);
-          while ((en.x & 31u) == static_cast<unsigned>(j)) {
-            const float2 x = Ef[en.x >> 5];
+          for (int k = 0; k < cj; ++k) {
+            const uint2 en = TS ? ge[e + k] : __ldg(ge + e + k);
+            const float2 x = Ef[en.x];
             const float w = __uint_as_float(en.y);
             sum.x = fmaf(w, x.x, sum.x);
             sum.y = fmaf(w, x.y, sum.y);
-            ++e;
-            en = TS ? sgent[e] : __ldg(gent + e);
           }
+          e += cj;
           v[j] = sum;
         }
       }
@@ -403,8 +412,12 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
   float2* tw = Z + GROUPS * G::ZG;                     // [N2][N1] twiddles
   float2* pixs = tw + N;                               // [4] calibrator pixels of the step
   float2* Es = pixs + 4;                               // [F][Na] gain-corrected voltages
-  int* sgofs = reinterpret_cast<int*>(Es + F * A.n_ant);  // [rows_alloc * N1] (TS)
-  uint2* sgent = reinterpret_cast<uint2*>(sgofs + ((A.rows_alloc * N1 + 1) & ~1));  // [gmax]
+  // gather table (TS): lane group lengths [rows_alloc * N1] (16-byte
+  // aligned), lane offsets [rows_alloc * N1], entries [gmax]
+  uint4* sgcnt = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(Es + F * A.n_ant) + 15) &
+                                          ~static_cast<uintptr_t>(15));
+  int* sgofs = reinterpret_cast<int*>(sgcnt + A.rows_alloc * N1);
+  uint2* sgent = reinterpret_cast<uint2*>(sgofs + ((A.rows_alloc * N1 + 1) & ~1));
 
   const int tid = threadIdx.x;
   float2* zg = Z + (tid / N1) * G::ZG;
@@ -423,11 +436,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
     const int4 wn = __ldg(A.win4 + c);
     const int span = wn.y > wn.w ? wn.y : wn.w;          // occupied rows / columns
     if (span <= N1 * (N2 / 4))
-      fused_unit<N, MAXA, N2 / 4, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2 / 4, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgcnt, sgent);
     else if (span <= N1 * (N2 / 2))
-      fused_unit<N, MAXA, N2 / 2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2 / 2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgcnt, sgent);
     else
-      fused_unit<N, MAXA, N2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgent);
+      fused_unit<N, MAXA, N2, TS, F>(A, c, t0, t1, Tt, zg, tw, pixs, Es, sgofs, sgcnt, sgent);
   }
 }
 
@@ -887,8 +900,8 @@ size_t image_smem_bytes(int n, int n_ant, int rs, int steps) {
 }
 
 size_t image_table_bytes(int rows_alloc, int n1, long long gmax) {
-  return static_cast<size_t>((rows_alloc * n1 + 1) & ~1) * sizeof(int) +
-         static_cast<size_t>(gmax) * sizeof(uint2);
+  return 16 + static_cast<size_t>(rows_alloc) * n1 * sizeof(uint4) +
+         static_cast<size_t>((rows_alloc * n1 + 1) & ~1) * sizeof(int) + static_cast<size_t>(gmax) * sizeof(uint2);
 }
 
 int image_fft_lanes(int n) {

@@ -103,6 +103,7 @@ struct PipeSmem {
   float2* prow;    // [rows_alloc] calibrator-pixel weight of each window row
   uint64_t* bars;  // full[2], empty[2]
   int* abort_flag;
+  uint4* sgcnt;    // [rows_alloc * N1] gather group lengths (TS)
   int* sgofs;      // [rows_alloc * N1] gather offsets (TS)
   uint2* sgent;    // [gmax] gather entries (TS)
 };
@@ -122,13 +123,17 @@ __device__ __forceinline__ long long producer_unit(const ImageArgs& A, const Pip
   const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
   const int gb = __ldg(A.gbase + c);
   const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * kN1;
+  const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * kN1;
   const uint2* gent = A.gent + gb;
 
   if constexpr (TS) {
     named_sync(kBarProd, kProdThreads);           // previous unit's gathers are done
     const int gn = __ldg(A.gbase + c + 1) - gb;
     for (int i = tid; i < gn; i += kProdThreads) S.sgent[i] = __ldg(gent + i);
-    for (int i = tid; i < R * kN1; i += kProdThreads) S.sgofs[i] = __ldg(gofs + i);
+    for (int i = tid; i < R * kN1; i += kProdThreads) {
+      S.sgofs[i] = __ldg(gofs + i);
+      S.sgcnt[i] = __ldg(gcnt + i);
+    }
   }
 
   // raw voltages of the unit's first frame
@@ -184,19 +189,23 @@ __device__ __forceinline__ long long producer_unit(const ImageArgs& A, const Pip
 #pragma unroll
       for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
       if (live) {
-        int e = TS ? S.sgofs[row * kN1 + n1] : __ldg(gofs + row * kN1 + n1);
-        uint2 en = TS ? S.sgent[e] : __ldg(gent + e);
+        const int li = row * kN1 + n1;
+        int e = TS ? S.sgofs[li] : __ldg(gofs + li);
+        const uint4 cw = TS ? S.sgcnt[li] : __ldg(gcnt + li);
+        const unsigned cv[4] = {cw.x, cw.y, cw.z, cw.w};
+        const uint2* ge = TS ? S.sgent : gent;
 #pragma unroll
         for (int j = 0; j < NZ; ++j) {
+          const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
           float2 sum = make_float2(0.f, 0.f);
-          while ((en.x & 31u) == static_cast<unsigned>(j)) {
-            const float2 x = Es[en.x >> 5];
+          for (int k = 0; k < cj; ++k) {
+            const uint2 en = TS ? ge[e + k] : __ldg(ge + e + k);
+            const float2 x = Es[en.x];
             const float w = __uint_as_float(en.y);
             sum.x = fmaf(w, x.x, sum.x);
             sum.y = fmaf(w, x.y, sum.y);
-            ++e;
-            en = TS ? S.sgent[e] : __ldg(gent + e);
           }
+          e += cj;
           v[j] = sum;
         }
       }
@@ -346,7 +355,9 @@ __global__ void __launch_bounds__(kBT, 1) epic_image_piped(const ImageArgs A) {
   S.prow = S.Er + 2 * Na;
   S.bars = reinterpret_cast<uint64_t*>(S.prow + A.rows_alloc);
   S.abort_flag = reinterpret_cast<int*>(S.bars + 4);
-  S.sgofs = S.abort_flag + 2;
+  S.sgcnt = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(S.abort_flag + 2) + 15) &
+                                     ~static_cast<uintptr_t>(15));
+  S.sgofs = reinterpret_cast<int*>(S.sgcnt + A.rows_alloc * kN1);
   S.sgent = reinterpret_cast<uint2*>(S.sgofs + ((A.rows_alloc * kN1 + 1) & ~1));
 
   const int tid = threadIdx.x;
@@ -416,7 +427,7 @@ size_t piped_smem_bytes(int n, int n_ant, int rs, int rows_alloc, long long gmax
               rows_alloc) * sizeof(float2);
   b = (b + 7) & ~static_cast<size_t>(7);
   b += 4 * sizeof(uint64_t) + 2 * sizeof(int);
-  if (gmax > 0) b += static_cast<size_t>((rows_alloc * kN1 + 1) & ~1) * sizeof(int) + static_cast<size_t>(gmax) * sizeof(uint2);
+  if (gmax > 0) b += image_table_bytes(rows_alloc, kN1, gmax);
   return b;
 }
 

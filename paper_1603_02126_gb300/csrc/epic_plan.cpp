@@ -91,6 +91,7 @@ struct epic_plan_s {
   DevBuf<int> d_gofs;           // [C][rows_alloc][N1] fused gather: first entry per FFT lane
   DevBuf<uint2> d_gent;         // fused gather entries (antenna << 5 | j, weight bits)
   DevBuf<int> d_gbase;          // [C + 1] first gather entry of each channel
+  DevBuf<uint4> d_gcnt;         // [C][rows_alloc][N1] gather group lengths (bytes)
   int gsmem = 0;                // fused gather table held in shared memory
   bool piped = false;           // fused path in its warp-specialised form
   int steps = 1;                // fused form: frames per step
@@ -193,6 +194,7 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.gofs = p->d_gofs.p;
   a.gent = p->d_gent.p;
   a.gbase = p->d_gbase.p;
+  a.gcnt = p->d_gcnt.p;
   a.gsmem = p->gsmem;
   a.piped = p->piped ? 1 : 0;
   a.steps = p->steps;
@@ -629,8 +631,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   if (fused && d->path == EPIC_PATH_PIPED && epic::piped_supported(N, Na)) {
     // warp-specialised form: two spectra slots; gather table in shared
     // memory when it fits (entries per channel <= Na K^2 + one per FFT lane)
-    const long long gmax = static_cast<long long>(Na) * KK +
-                           static_cast<long long>(p->rows_alloc) * epic::image_fft_lanes(N);
+    const long long gmax = static_cast<long long>(Na) * KK;   // entries per channel <= Na K^2
     const size_t s1 = epic::piped_smem_bytes(N, Na, p->rs_fused, p->rows_alloc, gmax);
     const size_t s0 = epic::piped_smem_bytes(N, Na, p->rs_fused, p->rows_alloc, 0);
     if (s1 <= static_cast<size_t>(smem_optin)) {
@@ -649,10 +650,10 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   }
   if (fused && !p->piped) {
     // shape preference: two frames per step, then one; the gather table in
-    // shared memory when it fits (entries per channel <= Na K^2 taps + one
-    // sentinel per FFT lane), else read through L1
+    // shared memory when it fits (entries per channel <= Na K^2 taps), else
+    // read through L1
     const int n1 = epic::image_fft_lanes(N);
-    const long long gmax = static_cast<long long>(Na) * KK + static_cast<long long>(p->rows_alloc) * n1;
+    const long long gmax = static_cast<long long>(Na) * KK;
     const size_t tab = epic::image_table_bytes(p->rows_alloc, n1, gmax);
     bool placed = false;
     for (int steps = epic::image_max_steps(N); steps >= 1 && !placed; --steps)
@@ -742,18 +743,21 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
     }
   // fused path: per FFT lane (window row r, lane n1 = x mod N1) the taps on
-  // its columns x = n1 + N1 j, sorted by j, then a sentinel entry (j = 31)
+  // its columns x = n1 + N1 j, grouped by j; the group lengths as bytes
   std::vector<int> gofs, gbase;
+  std::vector<uint4> gcnt;
   std::vector<uint2> gent;
   if (p->path == EPIC_PATH_FUSED) {
     const int N1 = epic::image_fft_lanes(N);
+    const int N2 = N / N1;
     const int RA = p->rows_alloc;
     gofs.assign(static_cast<size_t>(C) * RA * N1, 0);
-    std::vector<std::vector<std::pair<unsigned, float>>> lists(static_cast<size_t>(RA) * N1);
+    gcnt.assign(static_cast<size_t>(C) * RA * N1, make_uint4(0, 0, 0, 0));
+    std::vector<std::vector<std::pair<int, float>>> bucket(static_cast<size_t>(RA) * N1 * N2);
     gbase.assign(static_cast<size_t>(C) + 1, 0);
     for (int c = 0; c < C; ++c) {
       gbase[c] = static_cast<int>(gent.size());
-      for (auto& l : lists) l.clear();
+      for (auto& l : bucket) l.clear();
       for (int a = 0; a < Na; ++a) {
         if (p->flags[a]) continue;
         const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
@@ -764,24 +768,29 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
             const float w = wf[dy * K + dx];
             if (w == 0.0f) continue;
             const int x = x0w + dx;
-            lists[static_cast<size_t>(r0 + dy) * N1 + x % N1].emplace_back(
-                (static_cast<unsigned>(a) << 5) | static_cast<unsigned>(x / N1), w);
+            bucket[(static_cast<size_t>(r0 + dy) * N1 + x % N1) * N2 + x / N1].emplace_back(a, w);
           }
       }
       for (int li = 0; li < RA * N1; ++li) {
-        auto& l = lists[li];
-        std::stable_sort(l.begin(), l.end(), [](const std::pair<unsigned, float>& u,
-                                                const std::pair<unsigned, float>& v) {
-          return (u.first & 31u) < (v.first & 31u);
-        });
         gofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(gent.size()) - gbase[c];
-        for (const auto& en : l) {
-          uint2 q;
-          q.x = en.first;
-          std::memcpy(&q.y, &en.second, sizeof(float));
-          gent.push_back(q);
+        unsigned char cnt[16] = {0};
+        for (int j = 0; j < N2; ++j) {
+          const auto& l = bucket[static_cast<size_t>(li) * N2 + j];
+          if (l.size() > 255) {
+            epic_plan_destroy(p);
+            return fail(EPIC_ERR_UNSUPPORTED, "fused path: more than 255 gridding taps on one grid cell");
+          }
+          cnt[j] = static_cast<unsigned char>(l.size());
+          for (const auto& en : l) {
+            uint2 q;
+            q.x = static_cast<unsigned>(en.first);
+            std::memcpy(&q.y, &en.second, sizeof(float));
+            gent.push_back(q);
+          }
         }
-        gent.push_back(make_uint2(31u, 0u));
+        uint4 cw;
+        std::memcpy(&cw, cnt, sizeof(cw));
+        gcnt[static_cast<size_t>(c) * RA * N1 + li] = cw;
       }
     }
     gbase[C] = static_cast<int>(gent.size());
@@ -833,7 +842,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                       up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
                       up(p->d_cellf, cellf), up(p->d_pixph, pixph), up(p->d_rowcol, rowcol),
                       up(p->d_order, order), up(p->d_ranges, ranges), up(p->d_gofs, gofs),
-                      up(p->d_gent, gent), up(p->d_gbase, gbase)};
+                      up(p->d_gent, gent), up(p->d_gbase, gbase), up(p->d_gcnt, gcnt)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -866,6 +875,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_gofs.release();
   p->d_gent.release();
   p->d_gbase.release();
+  p->d_gcnt.release();
   p->d_pixph.release();
   p->d_rowcol.release();
   p->d_order.release();
