@@ -138,8 +138,12 @@ struct UnfusedArgs {
   const float* vscale;     // [C] or nullptr
   const int2* win;         // [C] (y0, rows)
   const float2* twid;      // [N]
-  float2* grid;            // scratch [nt*C][rows_alloc][N]
+  float2* grid;            // precision form: scratch [nt*C][rows_alloc][N] grid window
   float2* spec;            // scratch [nt*C][N][rs] transposed row spectra
+  const int* gofs;         // [C][rows_alloc][N1] first gather entry of each row-FFT lane
+  const uint4* gcnt;       // [C][rows_alloc][N1][ceil(N2/16)] entries per column group (bytes)
+  const uint2* gent;       // gather entries (antenna, weight bits), lane by lane, by group
+  const int* gbase;        // [C + 1] first entry of each channel
   float2* pix;             // scratch [nt*C] calibrator pixel per frame
   int rows_alloc, rs;
   double* image;           // [C][N][N]
@@ -151,6 +155,9 @@ struct UnfusedArgs {
   int cols_target;         // column-FFT work units per SM to aim for
 };
 bool unfused_supported(int n);
+// Lanes per row FFT (N1) of the unfused kernels: absolute column x is gather
+// group j = x / N1 of lane x % N1.
+int unfused_fft_lanes(int n);
 cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s);
 

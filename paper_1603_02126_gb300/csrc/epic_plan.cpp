@@ -92,6 +92,10 @@ struct epic_plan_s {
   DevBuf<uint2> d_gent;         // fused gather entries (antenna << 5 | j, weight bits)
   DevBuf<int> d_gbase;          // [C + 1] first gather entry of each channel
   DevBuf<uint4> d_gcnt;         // [C][rows_alloc][N1] gather group lengths (bytes)
+  DevBuf<int> d_ugofs;          // unfused gather: [C][rows_alloc][N1] lane offsets
+  DevBuf<uint4> d_ugcnt;        // unfused gather: [C][rows_alloc][N1][ceil(N2/16)] group lengths
+  DevBuf<uint2> d_ugent;        // unfused gather entries (antenna, weight bits)
+  DevBuf<int> d_ugbase;         // [C + 1] first unfused gather entry of each channel
   int gsmem = 0;                // fused gather table held in shared memory
   bool piped = false;           // fused path in its warp-specialised form
   int steps = 1;                // fused form: frames per step
@@ -125,7 +129,7 @@ struct epic_plan_s {
   // path and unfused scratch
   int path = EPIC_PATH_FUSED;
   size_t workspace_budget = static_cast<size_t>(2) << 30;
-  DevBuf<float2> d_ws;          // [nt*C] x (rows_alloc*N + N*rs + 1)
+  DevBuf<float2> d_ws;          // unfused scratch: [nt*C] x (N*rs + 1)
   int ws_time = 0;              // time samples the scratch holds
 
   // differentiation form
@@ -263,8 +267,8 @@ epic_status image_cluster(epic_plan_t p, const void* d_volt, long long n_time, d
 // Plain unfused path: batches of time samples through the device scratch.
 epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, double* d_image) {
   const int C = p->nc, N = p->n;
-  const size_t per_t = static_cast<size_t>(C) *
-                       (static_cast<size_t>(p->rows_alloc) * N + static_cast<size_t>(N) * p->rs + 1);
+  // per time sample: row spectra [C][N][rs] and the calibrator pixel [C]
+  const size_t per_t = static_cast<size_t>(C) * (static_cast<size_t>(N) * p->rs + 1);
   long long nt = static_cast<long long>(p->workspace_budget / (per_t * sizeof(float2)));
   if (p->tune_nt > 0 && p->tune_nt < nt) nt = p->tune_nt;
   if (nt < 1) nt = 1;
@@ -295,9 +299,13 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   a.win = p->d_win.p;
   a.twid = p->d_twid.p;
   const size_t cap = static_cast<size_t>(p->ws_time) * C;
-  a.grid = p->d_ws.p;
-  a.spec = a.grid + cap * p->rows_alloc * N;
+  a.grid = nullptr;
+  a.spec = p->d_ws.p;
   a.pix = a.spec + cap * N * p->rs;
+  a.gofs = p->d_ugofs.p;
+  a.gcnt = p->d_ugcnt.p;
+  a.gent = p->d_ugent.p;
+  a.gbase = p->d_ugbase.p;
   a.rows_alloc = p->rows_alloc;
   a.rs = p->rs;
   a.image = d_image;
@@ -795,6 +803,58 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
     gbase[C] = static_cast<int>(gent.size());
   }
+  // unfused path: per row-FFT lane (window row, lane n1 = x mod N1, x the
+  // absolute column) the taps on its columns x = n1 + N1 j, grouped by j;
+  // the group lengths as bytes, ceil(N2 / 16) 16-byte words per lane
+  std::vector<int> ugofs, ugbase;
+  std::vector<uint4> ugcnt;
+  std::vector<uint2> ugent;
+  if (p->path == EPIC_PATH_UNFUSED) {
+    const int N1 = epic::unfused_fft_lanes(N);
+    const int N2 = N / N1, CW = (N2 + 15) / 16;
+    const int RA = p->rows_alloc;
+    ugofs.assign(static_cast<size_t>(C) * RA * N1, 0);
+    ugcnt.assign(static_cast<size_t>(C) * RA * N1 * CW, make_uint4(0, 0, 0, 0));
+    ugbase.assign(static_cast<size_t>(C) + 1, 0);
+    std::vector<std::vector<std::pair<int, float>>> bucket(static_cast<size_t>(RA) * N1 * N2);
+    for (int c = 0; c < C; ++c) {
+      ugbase[c] = static_cast<int>(ugent.size());
+      for (auto& l : bucket) l.clear();
+      for (int a = 0; a < Na; ++a) {
+        if (p->flags[a]) continue;
+        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+        const int r0 = p->base[ob + 1] - h - p->y0[c], xa = p->base[ob] - h;
+        const float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
+        for (int dy = 0; dy < K; ++dy)
+          for (int dx = 0; dx < K; ++dx) {
+            const float w = wf[dy * K + dx];
+            if (w == 0.0f) continue;
+            const int x = xa + dx;
+            bucket[(static_cast<size_t>(r0 + dy) * N1 + x % N1) * N2 + x / N1].emplace_back(a, w);
+          }
+      }
+      for (int li = 0; li < RA * N1; ++li) {
+        ugofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(ugent.size()) - ugbase[c];
+        unsigned char cnt[32] = {0};
+        for (int j = 0; j < N2; ++j) {
+          const auto& l = bucket[static_cast<size_t>(li) * N2 + j];
+          if (l.size() > 255) {
+            epic_plan_destroy(p);
+            return fail(EPIC_ERR_UNSUPPORTED, "unfused path: more than 255 gridding taps on one grid cell");
+          }
+          cnt[j] = static_cast<unsigned char>(l.size());
+          for (const auto& en : l) {
+            uint2 q;
+            q.x = static_cast<unsigned>(en.first);
+            std::memcpy(&q.y, &en.second, sizeof(float));
+            ugent.push_back(q);
+          }
+        }
+        std::memcpy(&ugcnt[(static_cast<size_t>(c) * RA * N1 + li) * CW], cnt, sizeof(uint4) * CW);
+      }
+    }
+    ugbase[C] = static_cast<int>(ugent.size());
+  }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
   // cluster path: stencil (top row, first column) in window coordinates,
   // antennas sorted by top row, and per CTA the sorted range whose stencil
@@ -842,7 +902,9 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                       up(p->d_twid, twid), up(p->d_flags, p->flags), up(p->d_win4, win4),
                       up(p->d_cellf, cellf), up(p->d_pixph, pixph), up(p->d_rowcol, rowcol),
                       up(p->d_order, order), up(p->d_ranges, ranges), up(p->d_gofs, gofs),
-                      up(p->d_gent, gent), up(p->d_gbase, gbase), up(p->d_gcnt, gcnt)};
+                      up(p->d_gent, gent), up(p->d_gbase, gbase), up(p->d_gcnt, gcnt),
+                      up(p->d_ugofs, ugofs), up(p->d_ugcnt, ugcnt), up(p->d_ugent, ugent),
+                      up(p->d_ugbase, ugbase)};
   for (cudaError_t x : es)
     if (x != cudaSuccess) {
       epic_plan_destroy(p);
@@ -876,6 +938,10 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_gent.release();
   p->d_gbase.release();
   p->d_gcnt.release();
+  p->d_ugofs.release();
+  p->d_ugcnt.release();
+  p->d_ugent.release();
+  p->d_ugbase.release();
   p->d_pixph.release();
   p->d_rowcol.release();
   p->d_order.release();

@@ -2,11 +2,11 @@
 //
 // Each step is its own kernel and hands its result to the next through HBM,
 // one batch of frames at a time (frame f = t_local * C + c):
-//   grid_scatter   gain correction (Eq. 8) + gridding (Eq. 9): every
-//                  (frame, antenna, stencil row) adds its K taps to the
-//                  grid window G[f][row][N] with global float atomics;
-//   rows_fft       N-point FFT of every occupied grid row, written
-//                  transposed into Hs[f][kx][row];
+//   rows_gather    per frame: gain correction (Eq. 8) of every antenna into
+//                  shared memory, then gridding (Eq. 9) as a gather straight
+//                  into the FFT lanes of every occupied grid row (host-planned
+//                  tap lists, no grid in device memory, no atomics) and the
+//                  N-point row FFT, written transposed into Hs[f][kx][row];
 //   cols_fft       N-point FFT of every column (Eq. 10), |E|^2 summed over
 //                  the batch's frames in registers and added to the image;
 //                  the owner of the calibrator pixel stores it per frame;
@@ -41,7 +41,90 @@ __device__ __forceinline__ float2 load_volt_u(const void* volt, int fmt, size_t 
   return __ldg(static_cast<const float2*>(volt) + idx);
 }
 
-// ---- gridding: one thread per (frame, stencil row, antenna) ----
+// ---- gridding + row FFTs: one CTA per frame at a time ----
+// Lane (window row, n1) of a row FFT sums w * E'_a over its tap list for
+// each column group j (absolute column n1 + N1 j); lists and group lengths
+// (one byte per j) come from the plan.  Whole warps step through the rows
+// together; rows past the window transform zeros and store nothing.
+template <int N>
+__global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) rows_gather_kernel(const UnfusedArgs A, long long t0, int nt) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
+  constexpr int GROUPS = kUBT / N1, GPW = 32 / N1;
+  constexpr int CW = (N2 + 15) / 16;               // uint4 words of group lengths per lane
+  using X = fft::Xchg<N1, N2>;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[GROUPS * X::ZG];
+  extern __shared__ float2 Es[];                   // [Na] E / g of the current frame
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[i];
+  const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
+  float2* z = zbuf + g * X::ZG;
+  const int C = A.n_chan, Na = A.n_ant;
+  const long long frames = static_cast<long long>(nt) * C;
+  // item = c * nt + tl: a CTA's consecutive items stay in one channel (its
+  // tap lists stay in L1)
+  for (long long it = blockIdx.x; it < frames; it += gridDim.x) {
+    const int c = static_cast<int>(it / nt);
+    const int tl = static_cast<int>(it - static_cast<long long>(c) * nt);
+    const size_t f = static_cast<size_t>(tl) * C + c;
+    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+    __syncthreads();                               // previous frame's gathers are done
+    for (int a = threadIdx.x; a < Na; a += kUBT) {
+      const size_t vidx = (static_cast<size_t>(t0 + tl) * C + c) * Na + a;
+      const float2 e = load_volt_u(A.volt, A.input_fmt, vidx);
+      Es[a] = cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.wgain + static_cast<size_t>(c) * Na + a));
+    }
+    __syncthreads();
+    const int R = __ldg(A.win + c).y;
+    const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
+    const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * N1 * CW;
+    const uint2* gent = A.gent + __ldg(A.gbase + c);
+    for (int rb = g - g % GPW; rb < R; rb += GROUPS) {
+      const int row = rb + g % GPW;
+      const bool live = row < R;
+      float2 v[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
+      if (live) {
+        const int li = row * N1 + n1;
+        int e = __ldg(gofs + li);
+        unsigned cv[4 * CW];
+#pragma unroll
+        for (int w = 0; w < CW; ++w) {
+          const uint4 q = __ldg(gcnt + static_cast<size_t>(li) * CW + w);
+          cv[4 * w] = q.x;
+          cv[4 * w + 1] = q.y;
+          cv[4 * w + 2] = q.z;
+          cv[4 * w + 3] = q.w;
+        }
+#pragma unroll
+        for (int j = 0; j < N2; ++j) {
+          const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
+          float2 sum = make_float2(0.f, 0.f);
+          for (int k = 0; k < cj; ++k) {
+            const uint2 en = __ldg(gent + e + k);
+            const float2 x = Es[en.x];
+            const float w = __uint_as_float(en.y);
+            sum.x = fmaf(w, x.x, sum.x);
+            sum.y = fmaf(w, x.y, sum.y);
+          }
+          e += cj;
+          v[j] = sum;
+        }
+      }
+      fft::fft_lanes<N1, N2>(v, n1, z, tw, kFull);
+      if (live) {
+        float2* dst = A.spec + f * N * A.rs + row;
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) dst[static_cast<size_t>(n1 + N1 * h + N2 * k1) * A.rs] = v[h * N1 + k1];
+      }
+    }
+  }
+}
+
+// ---- gridding by scatter (the precision form's grid window): one thread
+// per (frame, stencil row, antenna) ----
 __global__ void grid_scatter_kernel(const UnfusedArgs A, long long t0, int nt) {
   const int Na = A.n_ant, C = A.n_chan, K = A.support, N = A.grid_n;
   const long long items = static_cast<long long>(nt) * C * K * Na;
@@ -68,41 +151,6 @@ __global__ void grid_scatter_kernel(const UnfusedArgs A, long long t0, int nt) {
       atomicAdd(g + 2 * dx, wv * ec.x);
       atomicAdd(g + 2 * dx + 1, wv * ec.y);
     }
-  }
-}
-
-// ---- row FFTs: one N1-lane group per (frame, occupied row) ----
-template <int N>
-__global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) rows_fft_kernel(const UnfusedArgs A, int nt) {
-  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
-  constexpr int GROUPS = kUBT / N1;
-  using X = fft::Xchg<N1, N2>;
-  __shared__ float2 tw[N];
-  __shared__ float2 zbuf[GROUPS * X::ZG];
-  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
-  const unsigned gmask = fft::group_mask<N1>(lane);
-  float2* z = zbuf + g * X::ZG;
-  const int C = A.n_chan;
-  const long long pairs = static_cast<long long>(nt) * C * A.rows_alloc;
-  for (long long pr = static_cast<long long>(blockIdx.x) * GROUPS + g; pr < pairs;
-       pr += static_cast<long long>(gridDim.x) * GROUPS) {
-    const int row = static_cast<int>(pr % A.rows_alloc);
-    const long long f = pr / A.rows_alloc;
-    const int c = static_cast<int>(f % C);
-    if (row >= __ldg(A.win + c).y) continue;        // group-uniform
-    const float2* src = A.grid + (static_cast<size_t>(f) * A.rows_alloc + row) * N;
-    float2 v[N2];
-#pragma unroll
-    for (int j = 0; j < N2; ++j) v[j] = src[n1 + N1 * j];
-    fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
-    float2* dst = A.spec + static_cast<size_t>(f) * N * A.rs + row;
-#pragma unroll
-    for (int h = 0; h < H; ++h)
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) dst[static_cast<size_t>(n1 + N1 * h + N2 * k1) * A.rs] = v[h * N1 + k1];
   }
 }
 
@@ -212,18 +260,18 @@ dim3 correlate_grid(int n_chan, int n_ant, int nt, int sms) {
 
 template <int N>
 cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
-  const size_t gbytes = static_cast<size_t>(nt) * a.n_chan * a.rows_alloc * N * sizeof(float2);
-  cudaError_t e = cudaMemsetAsync(a.grid, 0, gbytes, s);
-  if (e != cudaSuccess) return e;
-  const long long items = static_cast<long long>(nt) * a.n_chan * a.support * a.n_ant;
-  long long gb = (items + 255) / 256;
-  if (gb > static_cast<long long>(sms) * 16) gb = static_cast<long long>(sms) * 16;
-  grid_scatter_kernel<<<static_cast<unsigned>(gb), 256, 0, s>>>(a, t0, nt);
   constexpr int GROUPS = kUBT / UCfg<N>::N1;
-  const long long pairs = static_cast<long long>(nt) * a.n_chan * a.rows_alloc;
-  long long rb = (pairs + GROUPS - 1) / GROUPS;
-  if (rb > static_cast<long long>(sms) * 8) rb = static_cast<long long>(sms) * 8;
-  rows_fft_kernel<N><<<static_cast<unsigned>(rb), kUBT, 0, s>>>(a, nt);
+  const size_t es_bytes = static_cast<size_t>(a.n_ant) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(rows_gather_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(es_bytes));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_gather_kernel<N>, kUBT, es_bytes);
+  if (e != cudaSuccess) return e;
+  const long long frames = static_cast<long long>(nt) * a.n_chan;
+  long long rb = static_cast<long long>(per_sm > 0 ? per_sm : 1) * sms;
+  if (rb > frames) rb = frames;
+  rows_gather_kernel<N><<<static_cast<unsigned>(rb), kUBT, es_bytes, s>>>(a, t0, nt);
   constexpr int CBLK = (N + GROUPS - 1) / GROUPS;
   const int base_units = a.n_chan * CBLK;
   int segs = 1;
@@ -238,6 +286,17 @@ cudaError_t launch_unfused_n(const UnfusedArgs& a, long long t0, int nt, int sms
 }  // namespace
 
 bool unfused_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
+int unfused_fft_lanes(int n) {
+  switch (n) {
+    case 32: return UCfg<32>::N1;
+    case 64: return UCfg<64>::N1;
+    case 128: return UCfg<128>::N1;
+    case 256: return UCfg<256>::N1;
+    case 512: return UCfg<512>::N1;
+    default: return 0;
+  }
+}
 
 cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
   const long long items = static_cast<long long>(nt) * a.n_chan * a.support * a.n_ant;
