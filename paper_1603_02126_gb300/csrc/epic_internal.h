@@ -138,7 +138,6 @@ struct UnfusedArgs {
   const float* vscale;     // [C] or nullptr
   const int2* win;         // [C] (y0, rows)
   const float2* twid;      // [N]
-  float2* grid;            // precision form: scratch [nt*C][rows_alloc][N] grid window
   float2* spec;            // scratch [nt*C][N][rs] transposed row spectra
   const int* gofs;         // [C][rows_alloc][N1] first gather entry of each row-FFT lane
   const uint4* gcnt;       // [C][rows_alloc][N1][ceil(N2/16)] entries per column group (bytes)
@@ -158,7 +157,6 @@ bool unfused_supported(int n);
 // Lanes per row FFT (N1) of the unfused kernels: absolute column x is gather
 // group j = x / N1 of lane x % N1.
 int unfused_fft_lanes(int n);
-cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s);
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s);
 
 // Thread-block-cluster imaging for N = 256 / 512, epic_cluster.cu.

@@ -146,7 +146,6 @@ struct epic_plan_s {
   int precision = EPIC_PREC_FP32;
   int kp = 0;                   // K extent of the DFT (2 x window rows, padded to 64)
   int tc_time = 0;              // time samples per batch
-  DevBuf<float2> d_tc_grid;     // [tc_time*C][rows_alloc][N]
   DevBuf<uint16_t> d_tc_hh;     // [C*N][tc_time][kp]
   DevBuf<uint16_t> d_tc_dft;    // [2N][kp]
   DevBuf<float> d_tc_scale;     // [tc_time*C]
@@ -299,7 +298,6 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   a.win = p->d_win.p;
   a.twid = p->d_twid.p;
   const size_t cap = static_cast<size_t>(p->ws_time) * C;
-  a.grid = nullptr;
   a.spec = p->d_ws.p;
   a.pix = a.spec + cap * N * p->rs;
   a.gofs = p->d_ugofs.p;
@@ -362,13 +360,11 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   const int C = p->nc, N = p->n;
   if (p->tc_time == 0) {
     const size_t per_t = static_cast<size_t>(C) *
-                         (static_cast<size_t>(p->rows_alloc) * N * sizeof(float2) +
-                          static_cast<size_t>(N) * p->kp * 2 + sizeof(float) + sizeof(float2));
+                         (static_cast<size_t>(N) * p->kp * 2 + 2 * sizeof(float) + sizeof(float2));
     long long nt = static_cast<long long>(p->workspace_budget / per_t);
     nt = std::max<long long>(1, std::min<long long>(nt, 128));
-    const size_t n_grid = static_cast<size_t>(nt) * C * p->rows_alloc * N;
     const size_t n_hh = static_cast<size_t>(C) * N * nt * p->kp;
-    cudaError_t es[] = {p->d_tc_grid.alloc(n_grid), p->d_tc_hh.alloc(n_hh),
+    cudaError_t es[] = {p->d_tc_hh.alloc(n_hh),
                         p->d_tc_dft.alloc(static_cast<size_t>(2) * N * p->kp),
                         p->d_tc_scale.alloc(static_cast<size_t>(2 * nt) * C),
                         p->d_tc_pix.alloc(static_cast<size_t>(nt) * C)};
@@ -411,8 +407,11 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   u.vscale = p->d_vscale.p;
   u.win = p->d_win.p;
   u.twid = p->d_twid.p;
-  u.grid = p->d_tc_grid.p;
   u.spec = nullptr;
+  u.gofs = p->d_ugofs.p;
+  u.gcnt = p->d_ugcnt.p;
+  u.gent = p->d_ugent.p;
+  u.gbase = p->d_ugbase.p;
   u.pix = p->d_tc_pix.p;
   u.rows_alloc = p->rows_alloc;
   u.rs = p->rs;
@@ -957,7 +956,6 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_stage_img.release();
   p->d_ws.release();
   p->d_dldw.release();
-  p->d_tc_grid.release();
   p->d_tc_hh.release();
   p->d_tc_dft.release();
   p->d_tc_scale.release();

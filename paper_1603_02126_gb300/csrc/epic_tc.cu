@@ -1,11 +1,13 @@
 // Reduced-precision EPIC imaging: the column transform of Eq. 10 as a
 // tensor-core GEMM (tcgen05, FP16 or BF16 operands, FP32 accumulation).
 //
-// Per batch of frames (frame f = t_local * C + c), after the FP32 gridding of
-// the plain path:
+// Per batch of frames (frame f = t_local * C + c):
 //   frame_scale  S_f = sum_a |w_a E_a| / Na, an upper bound of every row
 //                spectrum value; s_f = largest power of two with s_f S_f < 1;
-//   rows_lp      FP32 N-point FFT of each occupied grid row; the spectrum is
+//   rows_lp      per frame, E' = E / g (Eq. 8) into shared memory, FP32
+//                gridding (Eq. 9) as a gather straight into the FFT lanes of
+//                every occupied grid row (the plain path's tap lists) and the
+//                FP32 N-point row FFT; the spectrum is
 //                scaled by s_f, rounded to FP16/BF16 and stored K-major as
 //                Hh[c][kx][t][2 jw + (re, im)]; the calibrator pixel is
 //                summed in FP32 from the same spectra;
@@ -100,58 +102,98 @@ __global__ void frame_scale_kernel(const TcArgs A, long long t0, int nt) {
 
 // ---- FP32 row FFTs, low-precision K-major output, FP32 calibrator pixel ----
 template <int N, typename T>
-__global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, int nt) {
+__global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, long long t0, int nt) {
   constexpr int N1 = LCfg<N>::N1, N2 = LCfg<N>::N2, H = N2 / N1;
-  constexpr int GROUPS = kLBT / N1;
+  constexpr int GROUPS = kLBT / N1, GPW = 32 / N1;
+  constexpr int CW = (N2 + 15) / 16;               // uint4 words of group lengths per lane
   using X = fft::Xchg<N1, N2>;
   __shared__ float2 tw[N];
   __shared__ float2 zbuf[GROUPS * X::ZG];
+  extern __shared__ float2 Es[];                   // [Na] E / g of the current frame
   for (int i = threadIdx.x; i < N; i += kLBT) tw[i] = A.u.twid[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
-  const unsigned gmask = fft::group_mask<N1>(lane);
   float2* z = zbuf + g * X::ZG;
-  const int C = A.u.n_chan;
-  const int ra = A.u.rows_alloc;
-  const long long pairs = static_cast<long long>(nt) * C * ra;
+  const int C = A.u.n_chan, Na = A.u.n_ant;
   const int pn1 = A.u.k0x % N1, pq = A.u.k0x / N1;
   const int pslot = (pq % H) * N1 + pq / H;
   T* hh = static_cast<T*>(A.hh);
-  for (long long pr = static_cast<long long>(blockIdx.x) * GROUPS + g; pr < pairs;
-       pr += static_cast<long long>(gridDim.x) * GROUPS) {
-    const int row = static_cast<int>(pr % ra);
-    const long long f = pr / ra;
-    const int c = static_cast<int>(f % C);
-    const int tl = static_cast<int>(f / C);
+  const long long frames = static_cast<long long>(nt) * C;
+  // item = c * nt + tl: a CTA's consecutive items stay in one channel
+  for (long long it = blockIdx.x; it < frames; it += gridDim.x) {
+    const int c = static_cast<int>(it / nt);
+    const int tl = static_cast<int>(it - static_cast<long long>(c) * nt);
+    const size_t f = static_cast<size_t>(tl) * C + c;
+    const float vs = A.u.vscale ? __ldg(A.u.vscale + c) : 1.0f;
+    __syncthreads();                               // previous frame's gathers are done
+    for (int a = threadIdx.x; a < Na; a += kLBT) {
+      const float2 e = load_volt_tc(A.u.volt, A.u.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
+      Es[a] = fft::cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a));
+    }
+    __syncthreads();
     const int2 wn = __ldg(A.u.win + c);
-    if (row >= wn.y) continue;                      // group-uniform
-    const float2* src = A.u.grid + (static_cast<size_t>(f) * ra + row) * N;
-    float2 v[N2];
+    const int R = wn.y;
+    const int* gofs = A.u.gofs + static_cast<size_t>(c) * A.u.rows_alloc * N1;
+    const uint4* gcnt = A.u.gcnt + static_cast<size_t>(c) * A.u.rows_alloc * N1 * CW;
+    const uint2* gent = A.u.gent + __ldg(A.u.gbase + c);
+    const float sf = __ldg(A.fscale + f);
+    for (int rb = g - g % GPW; rb < R; rb += GROUPS) {
+      const int row = rb + g % GPW;
+      const bool live = row < R;
+      float2 v[N2];
 #pragma unroll
-    for (int j = 0; j < N2; ++j) v[j] = src[n1 + N1 * j];
-    fft::fft_lanes<N1, N2>(v, n1, z, tw, gmask);
-    const float s = __ldg(A.fscale + f);
+      for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
+      if (live) {
+        // gridding (Eq. 9) as a gather into this lane's columns n1 + N1 j
+        const int li = row * N1 + n1;
+        int e = __ldg(gofs + li);
+        unsigned cv[4 * CW];
 #pragma unroll
-    for (int h = 0; h < H; ++h)
+        for (int w = 0; w < CW; ++w) {
+          const uint4 q = __ldg(gcnt + static_cast<size_t>(li) * CW + w);
+          cv[4 * w] = q.x;
+          cv[4 * w + 1] = q.y;
+          cv[4 * w + 2] = q.z;
+          cv[4 * w + 3] = q.w;
+        }
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const int kx = n1 + N1 * h + N2 * k1;
-        const float2 x = v[h * N1 + k1];
-        T* dst = hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * row;
-        store_lp(dst, x.x * s, x.y * s);
+        for (int j = 0; j < N2; ++j) {
+          const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
+          float2 sum = make_float2(0.f, 0.f);
+          for (int k = 0; k < cj; ++k) {
+            const uint2 en = __ldg(gent + e + k);
+            const float2 x = Es[en.x];
+            const float w = __uint_as_float(en.y);
+            sum.x = fmaf(w, x.x, sum.x);
+            sum.y = fmaf(w, x.y, sum.y);
+          }
+          e += cj;
+          v[j] = sum;
+        }
       }
-    if (A.u.do_cal && n1 == pn1) {
-      // pixel (k0x, k0y): sum over rows of X[jy][k0x] e^{+2 pi i jy k0y / N}
-      float2 x = make_float2(0.f, 0.f);
+      fft::fft_lanes<N1, N2>(v, n1, z, tw, fft::kFull);
+      if (live) {
 #pragma unroll
-      for (int q = 0; q < N2; ++q)
-        if (q == pslot) x = v[q];
-      const int jy = wn.x + row;
-      const float2 t = tw[(jy * A.u.k0y) & (N - 1)];
-      const float2 y = fft::cmul(x, t);
-      atomicAdd(&A.u.pix[f].x, y.x * A.u.pix_sign);
-      atomicAdd(&A.u.pix[f].y, y.y * A.u.pix_sign);
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const int kx = n1 + N1 * h + N2 * k1;
+            const float2 x = v[h * N1 + k1];
+            T* dst = hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * row;
+            store_lp(dst, x.x * sf, x.y * sf);
+          }
+        if (A.u.do_cal && n1 == pn1) {
+          // pixel (k0x, k0y): sum over rows of X[jy][k0x] e^{+2 pi i jy k0y / N}
+          float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < N2; ++q)
+            if (q == pslot) x = v[q];
+          const int jy = wn.x + row;
+          const float2 t = tw[(jy * A.u.k0y) & (N - 1)];
+          const float2 y = fft::cmul(x, t);
+          atomicAdd(&A.u.pix[f].x, y.x * A.u.pix_sign);
+          atomicAdd(&A.u.pix[f].y, y.y * A.u.pix_sign);
+        }
+      }
     }
   }
 }
@@ -419,12 +461,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 template <int N, typename T>
-cudaError_t rows_lp_n(const TcArgs& a, int nt, int sms, cudaStream_t s) {
-  constexpr int GROUPS = kLBT / LCfg<N>::N1;
-  const long long pairs = static_cast<long long>(nt) * a.u.n_chan * a.u.rows_alloc;
-  long long rb = (pairs + GROUPS - 1) / GROUPS;
-  if (rb > static_cast<long long>(sms) * 8) rb = static_cast<long long>(sms) * 8;
-  rows_lp_kernel<N, T><<<static_cast<unsigned>(rb), kLBT, 0, s>>>(a, nt);
+cudaError_t rows_lp_n(const TcArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
+  const size_t es_bytes = static_cast<size_t>(a.u.n_ant) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(rows_lp_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(es_bytes));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_lp_kernel<N, T>, kLBT, es_bytes);
+  if (e != cudaSuccess) return e;
+  const long long frames = static_cast<long long>(nt) * a.u.n_chan;
+  long long rb = static_cast<long long>(per_sm > 0 ? per_sm : 1) * sms;
+  if (rb > frames) rb = frames;
+  rows_lp_kernel<N, T><<<static_cast<unsigned>(rb), kLBT, es_bytes, s>>>(a, t0, nt);
   return cudaGetLastError();
 }
 
@@ -446,18 +494,15 @@ cudaError_t tc_prepare(bool bf16, size_t smem) {
 
 cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_data, long long t0, int nt,
                             int sms, cudaStream_t s) {
-  const size_t gbytes = static_cast<size_t>(nt) * a.u.n_chan * a.u.rows_alloc * a.u.grid_n * sizeof(float2);
-  cudaError_t e = cudaMemsetAsync(a.u.grid, 0, gbytes, s);
-  if (e == cudaSuccess && a.u.do_cal)
-    e = cudaMemsetAsync(a.u.pix, 0, static_cast<size_t>(nt) * a.u.n_chan * sizeof(float2), s);
-  if (e != cudaSuccess) return e;
-  e = launch_grid_scatter(a.u, t0, nt, sms, s);
+  cudaError_t e = cudaSuccess;
+  if (a.u.do_cal) e = cudaMemsetAsync(a.u.pix, 0, static_cast<size_t>(nt) * a.u.n_chan * sizeof(float2), s);
   if (e != cudaSuccess) return e;
   const int frames = nt * a.u.n_chan;
   frame_scale_kernel<<<(frames * 32 + 255) / 256, 256, 0, s>>>(a, t0, nt);
-  if (a.bf16) e = (a.u.grid_n == 128) ? rows_lp_n<128, __nv_bfloat16>(a, nt, sms, s)
-                                      : rows_lp_n<256, __nv_bfloat16>(a, nt, sms, s);
-  else e = (a.u.grid_n == 128) ? rows_lp_n<128, __half>(a, nt, sms, s) : rows_lp_n<256, __half>(a, nt, sms, s);
+  if (a.bf16) e = (a.u.grid_n == 128) ? rows_lp_n<128, __nv_bfloat16>(a, t0, nt, sms, s)
+                                      : rows_lp_n<256, __nv_bfloat16>(a, t0, nt, sms, s);
+  else e = (a.u.grid_n == 128) ? rows_lp_n<128, __half>(a, t0, nt, sms, s)
+                               : rows_lp_n<256, __half>(a, t0, nt, sms, s);
   if (e != cudaSuccess) return e;
   const int MB = 2 * a.u.grid_n / kTile;
   const int grid = (sms / MB) * MB;

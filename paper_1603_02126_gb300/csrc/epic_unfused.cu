@@ -123,37 +123,6 @@ __global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) rows_gather_kernel(c
   }
 }
 
-// ---- gridding by scatter (the precision form's grid window): one thread
-// per (frame, stencil row, antenna) ----
-__global__ void grid_scatter_kernel(const UnfusedArgs A, long long t0, int nt) {
-  const int Na = A.n_ant, C = A.n_chan, K = A.support, N = A.grid_n;
-  const long long items = static_cast<long long>(nt) * C * K * Na;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long it = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; it < items;
-       it += stride) {
-    const int a = static_cast<int>(it % Na);
-    long long r = it / Na;
-    const int dy = static_cast<int>(r % K);
-    r /= K;
-    const int c = static_cast<int>(r % C);
-    const int tl = static_cast<int>(r / C);
-    const int c0 = __ldg(A.cell0 + static_cast<size_t>(c) * Na + a);
-    if (c0 < 0) continue;
-    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
-    const size_t vidx = (static_cast<size_t>(t0 + tl) * C + c) * Na + a;
-    const float2 e = load_volt_u(A.volt, A.input_fmt, vidx);
-    const float2 ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.wgain + static_cast<size_t>(c) * Na + a));
-    const float* w = A.wts + (static_cast<size_t>(c) * Na + a) * K * K + dy * K;
-    const size_t f = static_cast<size_t>(tl) * C + c;
-    float* g = reinterpret_cast<float*>(A.grid + f * A.rows_alloc * N + c0 + dy * N);
-    for (int dx = 0; dx < K; ++dx) {
-      const float wv = __ldg(w + dx);
-      atomicAdd(g + 2 * dx, wv * ec.x);
-      atomicAdd(g + 2 * dx + 1, wv * ec.y);
-    }
-  }
-}
-
 // ---- column FFTs + |E|^2: unit = (channel, block of GROUPS columns, time segment) ----
 template <int N>
 __global__ void __launch_bounds__(kUBT, (N <= 256 ? 2 : 1)) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
@@ -296,14 +265,6 @@ int unfused_fft_lanes(int n) {
     case 512: return UCfg<512>::N1;
     default: return 0;
   }
-}
-
-cudaError_t launch_grid_scatter(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
-  const long long items = static_cast<long long>(nt) * a.n_chan * a.support * a.n_ant;
-  long long gb = (items + 255) / 256;
-  if (gb > static_cast<long long>(sms) * 16) gb = static_cast<long long>(sms) * 16;
-  grid_scatter_kernel<<<static_cast<unsigned>(gb), 256, 0, s>>>(a, t0, nt);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s) {
