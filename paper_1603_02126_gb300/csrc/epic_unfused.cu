@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 4 : 2)) rows_gather_kernel(c
 
 // ---- column FFTs + |E|^2: unit = (channel, block of GROUPS columns, time segment) ----
 template <int N>
-__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : (N <= 256 ? 2 : 1))) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
+__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_fft_kernel(const UnfusedArgs A, int nt, int segs) {
   constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
   constexpr int GROUPS = kUBT / N1;
   constexpr int CBLK = (N + GROUPS - 1) / GROUPS;   // column blocks per channel
