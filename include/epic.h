@@ -114,10 +114,13 @@ typedef struct {
 
 /* Build the gridding tables of Eq. 9 for every (channel, antenna): the
  * stencil centre is the nearest cell to u_a/du + N/2 (u_a = r_a f / c),
- * taps are normalised to sum 1 (W(0) = 1, Sec. 2.1).  Uploads tables and
- * sets all gains to 1.  Synchronous.  *out receives the plan.
+ * taps are normalised to sum 1 (W(0) = 1, Sec. 2.1).  The kernels grid by
+ * gathering: the plan also lists, for every FFT lane, the taps that land on
+ * its grid cells (at most 255 taps on one cell).  Uploads tables and sets
+ * all gains to 1.  Synchronous.  *out receives the plan.
  * Errors: INVALID_ARG (sizes, enums, NULL arrays), GRID_TOO_SMALL,
- * UNSUPPORTED (N or Na outside the built kernels), CUDA, OOM. */
+ * UNSUPPORTED (N or Na outside the built kernels, or more than 255 taps on
+ * one grid cell), CUDA, OOM. */
 epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* desc);
 
 /* Free the plan and its device memory (waits for its stream). NULL is OK. */

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace epic {
 namespace fft {
 
@@ -40,15 +42,40 @@ __host__ __device__ constexpr float cos32(int m) {
        : cos32_q(((m % 32) + 32) % 32);
 }
 
-// v * e^{+2 pi i k / R}; k is a compile-time constant after unrolling.
-template <int R>
-__device__ __forceinline__ float2 twiddle(float2 v, int k) {
-  const int m = ((k * (32 / R)) % 32 + 32) % 32;
-  if (m == 0) return v;
-  if (m == 8) return make_float2(-v.y, v.x);
-  if (m == 16) return make_float2(-v.x, -v.y);
-  if (m == 24) return make_float2(v.y, -v.x);
-  return cmul(v, make_float2(cos32(m), cos32(8 - m)));
+// v * e^{+2 pi i K / R}, K a template argument: the quarter turns are
+// swaps and sign flips, any other angle one complex multiply by exact
+// constants.  (With k a run-time argument the compiler kept the case split
+// as branches, even inside fully unrolled loops.)
+template <int R, int K>
+__device__ __forceinline__ float2 twiddle(float2 v) {
+  constexpr int m = ((K * (32 / R)) % 32 + 32) % 32;
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (m == 8) {
+    return make_float2(-v.y, v.x);
+  } else if constexpr (m == 16) {
+    return make_float2(-v.x, -v.y);
+  } else if constexpr (m == 24) {
+    return make_float2(v.y, -v.x);
+  } else {
+    constexpr float c = cos32(m), s = cos32(8 - m);
+    return cmul(v, make_float2(c, s));
+  }
+}
+
+// Radix-2 combination x[k] = e[k] + w^k o[k], x[k + R/2] = e[k] - w^k o[k]
+// for k = 0 .. R/2 - 1, expanded at compile time.
+template <int R, int K>
+__device__ __forceinline__ void butterfly(float2 (&x)[R], const float2 (&e)[R / 2], const float2 (&o)[R / 2]) {
+  const float2 t = twiddle<R, K>(o[K]);
+  x[K] = cadd(e[K], t);
+  x[K + R / 2] = csub(e[K], t);
+}
+
+template <int R, int... K>
+__device__ __forceinline__ void combine(float2 (&x)[R], const float2 (&e)[R / 2], const float2 (&o)[R / 2],
+                                        std::integer_sequence<int, K...>) {
+  (butterfly<R, K>(x, e, o), ...);
 }
 
 // In-register DFT with the '+' sign of Eq. 10, natural order in and out
@@ -64,12 +91,7 @@ struct Dft {
     }
     Dft<R / 2>::run(e);
     Dft<R / 2>::run(o);
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      const float2 t = twiddle<R>(o[k], k);
-      x[k] = cadd(e[k], t);
-      x[k + R / 2] = csub(e[k], t);
-    }
+    combine<R>(x, e, o, std::make_integer_sequence<int, R / 2>{});
   }
 };
 template <>
@@ -98,12 +120,7 @@ struct DftP {
       }
       DftP<R / 2, (NZ + 1) / 2>::run(e);
       DftP<R / 2, NZ / 2>::run(o);
-#pragma unroll
-      for (int k = 0; k < R / 2; ++k) {
-        const float2 t = twiddle<R>(o[k], k);
-        x[k] = cadd(e[k], t);
-        x[k + R / 2] = csub(e[k], t);
-      }
+      combine<R>(x, e, o, std::make_integer_sequence<int, R / 2>{});
     }
   }
 };

@@ -292,3 +292,23 @@ def test_image_many_units_per_cta(armed):
     oplan = O.Plan(w["ant_xy"], w["freqs"], 128, 0.5)
     ref, _ = O.image_interval(oplan, Eint, np.ones((1, 256)))
     assert _rel(img, ref) <= IMG_TOL
+
+
+@pytest.mark.parametrize("path", ["fused", "unfused"])
+def test_gather_limit_255_taps_per_cell(path):
+    """The gather lists hold at most 255 taps per grid cell: 255 co-located
+    antennas still image exactly (every tap of the 3x3 stencil lands 255
+    times on the same cell), 256 are refused with UNSUPPORTED."""
+    from paper_1603_02126_gb300 import Plan
+    from paper_1603_02126_gb300._binding import EpicError
+    rng = np.random.default_rng(255)
+    freqs = [50e6]
+    ant = np.tile([[3.0, -2.0]], (255, 1))
+    E = (rng.standard_normal((5, 1, 255)) + 1j * rng.standard_normal((5, 1, 255))).astype(np.complex64)
+    p = Plan(ant, freqs, 32, 0.5, input="c64", path=path)
+    img = p.image(torch.from_numpy(E).cuda()).cpu().numpy()
+    ref, _ = O.image_interval(O.Plan(ant, freqs, 32, 0.5), E.astype(np.complex128), np.ones((1, 255)))
+    assert _rel(img, ref) <= IMG_TOL
+    with pytest.raises(EpicError) as ei:
+        Plan(np.tile([[3.0, -2.0]], (256, 1)), freqs, 32, 0.5, input="c64", path=path)
+    assert ei.value.status == 7
