@@ -1,0 +1,115 @@
+"""GPU parity at the full sizes of the precision and batching workloads, in
+the launch configuration the benchmark times, checked at sampled pixels and
+antennas against the oracle's single-pixel sums (the whole oracle image is
+out of reach at these sizes).
+
+  * Na = 1024 in a 200 m disc, 32 channels, N = 256, T = 4096 4-bit
+    samples: plain FP32 and the FP16 / BF16 tensor-core forms.
+  * Na = 2048 hexagonal array, 256 channels, N = 512, T = 4096 complex64
+    samples: the batching form (autotuned, one CUDA graph per interval).
+"""
+import numpy as np
+import pytest
+
+import epic_synth as synth
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = {"fp32": 1e-5, "fp16": 3e-3, "bf16": 3e-3}
+GAIN_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _gain_err(g, ref):
+    amp = np.max(np.abs(np.abs(g) - np.abs(ref)) / np.abs(ref))
+    ph = np.max(np.abs(np.angle(g * np.conj(ref))))
+    return amp, ph
+
+
+def _pixels(n, k0, rng, extra=5):
+    return [k0] + [(int(rng.integers(n)), int(rng.integers(n))) for _ in range(extra)] + [(0, n - 1)]
+
+
+def _check(img_c, ref, tol, exact):
+    """Relative L2 over the sampled pixels; FP32 also pixel by pixel."""
+    got = np.array([img_c[ky, kx] for kx, ky in ref[0]])
+    want = ref[1]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= tol
+    if exact:
+        for g_, w_ in zip(got, want):
+            assert abs(g_ - w_) <= tol * abs(w_) + 1e-6 * img_c.max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_compact1024_full_size_sampled(prec):
+    from paper_1603_02126_gb300 import Plan
+    w = synth.workload("compact1024")
+    v = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                 w["noise_power"], w["lsb"], seed=2)
+    C, Na = len(w["freqs"]), w["ant_xy"].shape[0]
+    p = Plan(w["ant_xy"], w["freqs"], 256, 0.5, support=3, param=0.5, input="ci4",
+             voltage_scale=w["lsb"], path="unfused", precision=prec, workspace_bytes=4 << 30)
+    p.configure((0.0, 0.0), w["model"], w["gamma"])
+    img = p.image(v).cpu().numpy()
+    gout = torch.zeros((C, Na), dtype=torch.complex128, device="cuda")
+    p.update(gout)
+    assert p.sync() == 0
+    g_gpu = gout.cpu().numpy()
+    rng = np.random.default_rng(7)
+    for c in (0, 31):
+        E = O.unpack_ci4(v[:, c:c + 1, :].cpu().numpy()) * w["lsb"][c]
+        sub = O.Plan(w["ant_xy"], [w["freqs"][c]], 256, 0.5, model_lmS=w["model"])
+        pix = _pixels(256, tuple(int(k) for k in sub.k0), rng)
+        ref = O.image_pixels(sub, E, np.ones((1, Na)), 0, pix, block=128)
+        _check(img[c], (pix, ref), IMG_TOL[prec], prec == "fp32")
+        ants = [0, 517, Na - 1]
+        Kc, P = O.correlate_sampled(sub, E, np.ones((1, Na)), 0, ants, block=128)
+        gs, _ = O.epical_update(Kc, P, sub.A0[0, ants], sub.D[0, ants], np.ones(3, complex),
+                                w["gamma"])
+        amp, ph = _gain_err(g_gpu[c, ants], gs)
+        assert amp <= GAIN_TOL and ph <= GAIN_TOL, (c, amp, ph)
+
+
+def test_hex2048_full_size_graph_sampled():
+    from paper_1603_02126_gb300 import Plan
+    w = synth.workload("hex2048")
+    v = synth.voltages_c64_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                 w["noise_power"], seed=3)
+    C, Na = len(w["freqs"]), w["ant_xy"].shape[0]
+    img = torch.empty((C, 512, 512), dtype=torch.float64, device="cuda")
+    gout = torch.empty((C, Na), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+    p = Plan(w["ant_xy"], w["freqs"], 512, 0.5, support=3, param=0.5, input="c64",
+             path="unfused", workspace_bytes=8 << 30, stream=stream.cuda_stream)
+    p.configure((0.0, 0.0), w["model"], w["gamma"])
+    with torch.cuda.stream(stream):
+        p.autotune(v[:256], img)
+        p.configure((0.0, 0.0), w["model"], w["gamma"])   # fresh accumulators and gains
+        p.graph_capture(v, img, gout)
+        p.graph_launch()
+    stream.synchronize()
+    assert p.sync() == 0
+    img_h = img.cpu().numpy()
+    g_gpu = gout.cpu().numpy()
+    rng = np.random.default_rng(11)
+    for c in (0, 255):
+        E = v[:, c:c + 1, :].cpu().numpy().astype(np.complex128)
+        sub = O.Plan(w["ant_xy"], [w["freqs"][c]], 512, 0.5, model_lmS=w["model"])
+        pix = _pixels(512, tuple(int(k) for k in sub.k0), rng)
+        ref = O.image_pixels(sub, E, np.ones((1, Na)), 0, pix, block=32)
+        _check(img_h[c], (pix, ref), IMG_TOL["fp32"], True)
+        ants = [0, 1023, Na - 1]
+        Kc, P = O.correlate_sampled(sub, E, np.ones((1, Na)), 0, ants, block=32)
+        gs, _ = O.epical_update(Kc, P, sub.A0[0, ants], sub.D[0, ants], np.ones(3, complex),
+                                w["gamma"])
+        amp, ph = _gain_err(g_gpu[c, ants], gs)
+        assert amp <= GAIN_TOL and ph <= GAIN_TOL, (c, amp, ph)
