@@ -60,8 +60,8 @@ int image_rs(int rows_alloc);
 int image_rs_fused(int rows_alloc);
 
 // Dynamic shared memory of the adjoint kernel (layout: window [rows][N],
-// spectra [N][rs], FFT exchange, twiddles).
-size_t adjoint_smem_bytes(int n, int rows_alloc, int rs);
+// spectra [N][rs], FFT exchange, twiddles, E' [Na]).
+size_t adjoint_smem_bytes(int n, int rows_alloc, int rs, int n_ant);
 // Row stride of the fused kernel's grid window, N + N1.
 int image_window_stride(int n);
 size_t image_smem_bytes(int n, int n_ant, int rs, int steps);
@@ -116,6 +116,10 @@ struct AdjointArgs {
   const float* vscale;
   const int2* win;
   const float2* twid;
+  const int* gofs;         // gridding gather (absolute columns): [C][rows_alloc][N1] lane offsets
+  const uint4* gcnt;       // [C][rows_alloc][N1] entries per column group (bytes)
+  const uint2* gent;       // entries (antenna, weight bits)
+  const int* gbase;        // [C + 1] first entry of each channel
   const double* dldi;      // [C][N][N] dL/dI
   double2* dldw;           // [C][Na] accumulated dL/dconj(w), pre-zeroed
   double img_scale;        // 1 / T

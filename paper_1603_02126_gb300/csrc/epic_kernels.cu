@@ -450,9 +450,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
 // conjugate gain multipliers is
 //   dL/dconj(w_a) = (1/T) sum_t conj(E_a(t)) sum_j W'_a(j) [F^- (R . X(t))]_j
 // (F^- = the conjugate transform).  Every frame is recomputed (nothing is
-// stored): scatter, row FFTs, column FFTs, multiply by R, inverse column
-// FFTs into the grid window, inverse row FFTs, gather of the K x K taps per
-// antenna.  R for the unit's channel stays in registers.
+// stored): gridding as a per-lane gather from E' in shared memory (the plan's
+// absolute-column tap lists) straight into the row FFTs, column FFTs,
+// multiply by R, inverse column FFTs into the grid window, inverse row FFTs,
+// degridding gather of the K x K taps per antenna.  E' of the next frame is
+// formed during the degridding.  R for the unit's channel stays in registers.
 template <int N, int MAXA>
 __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const AdjointArgs A) {
   using G = Geo<N>;
@@ -463,6 +465,7 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
   float2* Tt = Wg + A.rows_alloc * N;                  // [N][rs] or [rows][N]
   float2* Z = Tt + N * A.rs;
   float2* tw = Z + GROUPS * G::ZG;
+  float2* Es = tw + N;                                 // [Na] E / g of the current frame
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -472,14 +475,11 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
   float2* zg = Z + g * G::ZG;
 
   for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
-  for (int i = tid; i < A.rows_alloc * N; i += BT) Wg[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const int Na = A.n_ant;
   const int K = A.support;
   const int KK = K * K;
-  const int items = K * Na;
-  const int items_pad = ((items + BT - 1) / BT) * BT;
   const long long T = A.n_time;
   const int units = A.n_chan * A.segs;
 
@@ -496,6 +496,9 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
     const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
     const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
     const double* rimg = A.dldi + static_cast<size_t>(c) * N * N;
+    const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
+    const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * N1;
+    const uint2* gent = A.gent + __ldg(A.gbase + c);
 
     // R_k for this thread's pixels, in the column-FFT output order
     float rk[G::NACC];
@@ -510,50 +513,45 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
           rk[r * N2 + h * N1 + k1] = static_cast<float>(__ldg(rimg + ky * N + kx));
         }
     }
+    // raw voltages (scaled) of the unit's first frame and its E' = E / g
     float2 gac[MAXA], ecur[MAXA];
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
+      const int a = tid + BT * i;
       gac[i] = make_float2(0.f, 0.f);
       ecur[i] = make_float2(0.f, 0.f);
+      if (a < Na) {
+        const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t0, c, a);
+        ecur[i] = make_float2(e.x * vs, e.y * vs);
+        Es[a] = cmul(ecur[i], __ldg(wg + a));
+      }
     }
+    __syncthreads();
 
     for (long long t = t0; t < t1; ++t) {
-      // ---- A: raw voltages, gain + scatter (as the forward pass) ----
-#pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        const int a = tid + BT * i;
-        if (a < Na) {
-          const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t, c, a);
-          ecur[i] = make_float2(e.x * vs, e.y * vs);
-        }
-      }
-      for (int it = tid; it < items_pad; it += BT) {
-        const bool in = it < items;
-        const int a = in ? it % Na : 0;
-        const int dy = in ? it / Na : 0;
-        const int c0 = in ? __ldg(cell0 + a) : -1;
-        if (c0 >= 0) {
-          const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t, c, a);
-          const float2 ec = cmul(make_float2(e.x * vs, e.y * vs), __ldg(wg + a));
-          const float* wrow = wts + static_cast<size_t>(a) * KK + dy * K;
-          const int rowcell = c0 + dy * N;
-          for (int dx = 0; dx < K; ++dx) {
-            const float w = __ldg(wrow + dx);
-            atomicAdd(&Wg[rowcell + dx].x, w * ec.x);
-            atomicAdd(&Wg[rowcell + dx].y, w * ec.y);
-          }
-        }
-      }
-      __syncthreads();
-
-      // ---- B: row FFTs into the transposed buffer ----
+      // ---- B: gridding gather (Eq. 9, absolute columns n1 + N1 j) + row FFTs ----
       for (int row = g; row < R; row += GROUPS) {
         float2 v[N2];
-        float2* wr = Wg + row * N;
+        {
+          const int li = row * N1 + n1;
+          int e = __ldg(gofs + li);
+          const uint4 cw = __ldg(gcnt + li);
+          const unsigned cv[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
-        for (int j = 0; j < N2; ++j) v[j] = wr[n1 + N1 * j];
-#pragma unroll
-        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
+          for (int j = 0; j < N2; ++j) {
+            const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
+            float2 sum = make_float2(0.f, 0.f);
+            for (int k = 0; k < cj; ++k) {
+              const uint2 en = __ldg(gent + e + k);
+              const float2 x = Es[en.x];
+              const float w = __uint_as_float(en.y);
+              sum.x = fmaf(w, x.x, sum.x);
+              sum.y = fmaf(w, x.y, sum.y);
+            }
+            e += cj;
+            v[j] = sum;
+          }
+        }
         fft_group<N>(v, n1, zg, tw, gmask);
 #pragma unroll
         for (int h = 0; h < H; ++h)
@@ -607,8 +605,6 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
           const float2 x = wr[n1 + N1 * j];
           v[j] = make_float2(x.x, -x.y);
         }
-#pragma unroll
-        for (int j = 0; j < N2; ++j) wr[n1 + N1 * j] = make_float2(0.f, 0.f);
         fft_group<N>(v, n1, zg, tw, gmask);
 #pragma unroll
         for (int h = 0; h < H; ++h)
@@ -640,10 +636,16 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
             gac[i].x += e.x * yr + e.y * yi;     // conj(e) * y
             gac[i].y += e.x * yi - e.y * yr;
           }
+          // next frame's raw voltages and E' (the row pass reads Es after the barrier)
+          if (t + 1 < t1) {
+            const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t + 1, c, a);
+            ecur[i] = make_float2(e.x * vs, e.y * vs);
+            Es[a] = cmul(ecur[i], __ldg(wg + a));
+          }
         }
       }
+      __syncthreads();                                 // Tt and Es are rewritten next frame
     }
-    __syncthreads();
 #pragma unroll
     for (int i = 0; i < MAXA; ++i) {
       const int a = tid + BT * i;
@@ -863,7 +865,7 @@ int image_rs(int rows_alloc) {
   return rs;
 }
 
-size_t adjoint_smem_bytes(int n, int rows_alloc, int rs) {
+size_t adjoint_smem_bytes(int n, int rows_alloc, int rs, int n_ant) {
   int groups = 0, zg = 0;
   switch (n) {
     case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
@@ -872,9 +874,9 @@ size_t adjoint_smem_bytes(int n, int rows_alloc, int rs) {
     case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
     default: return 0;
   }
-  // grid window [rows][N], transposed / row-major spectra [N][rs], exchange, twiddles
+  // grid window [rows][N], transposed / row-major spectra [N][rs], exchange, twiddles, E' [Na]
   const size_t elems = static_cast<size_t>(rows_alloc) * n + static_cast<size_t>(n) * rs +
-                       static_cast<size_t>(groups) * zg + n;
+                       static_cast<size_t>(groups) * zg + n + n_ant;
   return elems * sizeof(float2);
 }
 

@@ -802,14 +802,15 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
     gbase[C] = static_cast<int>(gent.size());
   }
-  // unfused path: per row-FFT lane (window row, lane n1 = x mod N1, x the
-  // absolute column) the taps on its columns x = n1 + N1 j, grouped by j;
-  // the group lengths as bytes, ceil(N2 / 16) 16-byte words per lane
+  // unfused path and the fused path's adjoint: per row-FFT lane (window row,
+  // lane n1 = x mod N1, x the absolute column) the taps on its columns
+  // x = n1 + N1 j, grouped by j; the group lengths as bytes, ceil(N2 / 16)
+  // 16-byte words per lane
   std::vector<int> ugofs, ugbase;
   std::vector<uint4> ugcnt;
   std::vector<uint2> ugent;
-  if (p->path == EPIC_PATH_UNFUSED) {
-    const int N1 = epic::unfused_fft_lanes(N);
+  if (p->path == EPIC_PATH_UNFUSED || p->path == EPIC_PATH_FUSED) {
+    const int N1 = p->path == EPIC_PATH_UNFUSED ? epic::unfused_fft_lanes(N) : epic::image_fft_lanes(N);
     const int N2 = N / N1, CW = (N2 + 15) / 16;
     const int RA = p->rows_alloc;
     ugofs.assign(static_cast<size_t>(C) * RA * N1, 0);
@@ -1482,7 +1483,11 @@ epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_t
   a.rs = p->rs;
   const long long units = static_cast<long long>(p->nc) * a.segs;
   a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
-  a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs);
+  a.gofs = p->d_ugofs.p;
+  a.gcnt = p->d_ugcnt.p;
+  a.gent = p->d_ugent.p;
+  a.gbase = p->d_ugbase.p;
+  a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs, p->na);
   EPIC_CUDA(epic::launch_adjoint(p->n, a, p->stream));
   EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_flags.p,
                                           reinterpret_cast<double2*>(d_grad_g), p->stream));
