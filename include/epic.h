@@ -53,15 +53,15 @@ typedef enum { EPIC_KERNEL_GAUSSIAN = 0, EPIC_KERNEL_TOPHAT = 1 } epic_kernel_ty
 typedef enum { EPIC_IN_CI4 = 0, EPIC_IN_COMPLEX64 = 1 } epic_input_format;
 typedef enum { EPIC_PREC_FP32 = 0, EPIC_PREC_FP16 = 1, EPIC_PREC_BF16 = 2 } epic_precision;
 /* Kernel structure of epic_image.  FUSED: one persistent launch keeps each
- * frame in one SM (N <= 128).  UNFUSED: the plain path, grid and row
- * spectra pass through device memory in batches (N = 32..512).  CLUSTER:
+ * frame in one SM (N <= 128).  UNFUSED: the plain path, row spectra pass
+ * through device memory in batches (N = 32..512).  CLUSTER:
  * one persistent launch in which a thread-block cluster (8 CTAs for N = 256,
  * 16 for N = 512) shares each frame through distributed shared memory.
  * PIPED: the fused path in warp-specialised form (N = 64 or 128, Na <= 512):
  * producer warps grid and row-transform frame t + 1 while consumer warps
  * column-transform frame t, handing frames over through two shared-memory
- * slots (FUSED keeps the form with two CTA barriers per frame, measured
- * faster on this build).  AUTO picks FUSED for N <= 128, else UNFUSED
+ * slots (FUSED keeps the form with two CTA barriers per step of two
+ * frames, measured faster on this build).  AUTO picks FUSED for N <= 128, else UNFUSED
  * (measured faster than CLUSTER on this build). */
 typedef enum {
   EPIC_PATH_AUTO = 0, EPIC_PATH_FUSED = 1, EPIC_PATH_UNFUSED = 2, EPIC_PATH_CLUSTER = 3,

@@ -3,15 +3,18 @@
 // epic_image_fused<N>: one persistent launch images every frame (t, c) of a
 // batch.  A CTA owns one work unit (channel c, a contiguous time segment) at
 // a time and keeps that unit's running |E(s_k)|^2 sums in registers, so the
-// only HBM traffic per frame is the Na voltage bytes.  Per frame:
-//   A  unpack 4-bit voltages, multiply by 1/g (Eq. 8) and scatter the K x K
-//      weighted taps (Eq. 9) into a shared-memory grid window that spans only
-//      the occupied grid rows; lanes of a warp that hit the same cell are
-//      merged with __match_any_sync before the shared-memory atomic add;
-//   B  EPICal correlation of the previous frame (Eqs. 12, 15), then N-point
-//      row FFTs of the occupied rows, written transposed;
-//   C  N-point column FFTs (Eq. 10), |E|^2 accumulated in registers; the
-//      thread that owns the calibrator pixel stores it for the correlation.
+// only HBM traffic per frame is the Na voltage bytes.  The unit advances F
+// frames per step (F spectra slots in shared memory), two CTA barriers per
+// step:
+//   row pass     EPICal correlation of the previous step's frames (Eqs. 12,
+//                15); for every (frame, occupied grid row) the FFT lanes
+//                gather their gridding taps (Eq. 9) from E' = E / g (Eq. 8)
+//                in shared memory, then the N-point row FFT, written
+//                transposed into the frame's slot;
+//   column pass  N-point column FFTs (Eq. 10), |E|^2 accumulated in
+//                registers, the calibrator pixel stored for the correlation;
+//                then the next step's E' (4-bit unpack, gain) into shared
+//                memory.
 // The centring factor (-1)^(jx+jy) and the 1/Na of Eq. 10 are folded into
 // the gridding weights by the plan; (-1)^(kx+ky) only matters for the
 // calibrator pixel and is applied there.
