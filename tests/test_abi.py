@@ -77,6 +77,11 @@ def _desc(B, **over):
     (dict(precision=1, path=1), 7),
     (dict(grid_n=1024), 7),
     (dict(ant=[[60.0, 0.0], [0.0, 0.0]]), 2),
+    (dict(path=5), 1),                      # unknown path
+    (dict(path=4, grid_n=32), 7),           # warp-specialised form: N = 64 or 128 only
+    (dict(path=4, precision=2), 7),         # ... and FP32 only
+    (dict(path=3, grid_n=128), 7),          # cluster form: N = 256 or 512 only
+    (dict(path=3, grid_n=256, precision=1), 7),
 ])
 def test_create_rejects_on_host(lib, over, code):
     from paper_1603_02126_gb300 import _binding as B
