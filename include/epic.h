@@ -223,6 +223,17 @@ epic_status epical_configure(epic_plan_t plan, double cal_l, double cal_m,
  * Errors: STATE (not configured, or no frames since the last update). */
 epic_status epical_update(epic_plan_t plan, double* d_gains_out, int* d_status);
 
+/* Gains taken as constant across a band of channels (Sec. 4: the LWA
+ * demonstration averages the per-channel solutions across its central
+ * channels to raise the signal to noise).  For every unflagged antenna the
+ * gains of channels c_lo <= c < c_hi are replaced by their plain complex
+ * mean (and 1/g with them); other channels and flagged antennas are left as
+ * they are, and so is an antenna whose mean is zero or not finite.  Call
+ * after epical_update; the next epic_image uses the averaged gains.
+ * Asynchronous on the plan stream.
+ * Errors: INVALID_ARG (NULL plan, unless 0 <= c_lo < c_hi <= C), CUDA. */
+epic_status epical_average_channels(epic_plan_t plan, int c_lo, int c_hi);
+
 /* Wait for the plan's stream.  *n_held (may be NULL) receives the number
  * of held (antenna, channel) gains since the previous sync; the call
  * returns EPIC_ERR_NUMERIC if it is non-zero.  Synchronous. */

@@ -32,7 +32,7 @@ __all__ = [
     "cal_denominator", "correlate", "epical_update", "image_interval",
     "epical_interval", "visibilities", "visibility_solve", "gain_error",
     "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
-    "model_image", "chi2_loss", "chi2_gradient",
+    "model_image", "chi2_loss", "chi2_gradient", "average_channels",
 ]
 
 
@@ -285,6 +285,23 @@ def epical_update(Kc, P, A0, D, g, gamma: float, flags=None, d_min: float = 0.0)
         gn = (1.0 - gamma) * Cc / D + gamma * g
     held = flags | ~(np.abs(D) > d_min) | ~np.isfinite(gn)
     return np.where(held, g, gn), held
+
+
+def average_channels(g, c_lo: int, c_hi: int, flags=None):
+    """Gains assumed constant across a band of channels (Sec. 4, LWA data):
+    after an interval's update, every channel c_lo <= c < c_hi takes the
+    plain mean of the complex solutions of those channels, antenna by
+    antenna.  Channels outside the band, flagged antennas and antennas whose
+    mean is zero or not finite are returned unchanged.  g: [C][Na] complex."""
+    g = np.array(g, np.complex128, copy=True)
+    C, Na = g.shape
+    if not (0 <= c_lo < c_hi <= C):
+        raise ValueError("need 0 <= c_lo < c_hi <= C")
+    flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
+    mean = g[c_lo:c_hi].mean(axis=0)
+    use = ~flags & np.isfinite(mean) & (np.abs(mean) > 0)
+    g[c_lo:c_hi, use] = mean[use]
+    return g
 
 
 # --------------------------------------------------------------------------

@@ -24,7 +24,7 @@ EPIC_PATH_AUTO, EPIC_PATH_FUSED, EPIC_PATH_UNFUSED, EPIC_PATH_CLUSTER, EPIC_PATH
 EXPORTS = [
     "epic_plan_create", "epic_plan_destroy", "epic_plan_set_stream", "epic_plan_get_info",
     "epic_set_gains", "epic_image", "epic_image_host", "epic_image_host_static",
-    "epical_configure", "epical_update",
+    "epical_configure", "epical_update", "epical_average_channels",
     "epic_plan_sync", "epical_get_gains", "epical_get_state", "epical_set_state",
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
     "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
@@ -102,6 +102,7 @@ def load(path: str | None = None) -> ct.CDLL:
         "epic_image_host_static": [P, P, ct.c_longlong, P, ct.c_int],
         "epical_configure": [P, ct.c_double, ct.c_double, ct.c_int, c_dp, ct.c_double, c_dp],
         "epical_update": [P, P, P],
+        "epical_average_channels": [P, ct.c_int, ct.c_int],
         "epic_plan_sync": [P, c_ip],
         "epical_get_gains": [P, c_dp],
         "epical_get_state": [P, P, ct.POINTER(ct.c_size_t)],

@@ -231,6 +231,12 @@ class Plan:
         B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),
                                         _dptr(status, torch.int32, "status")))
 
+    def average_channels(self, c_lo, c_hi):
+        """Take the gains as constant across channels c_lo .. c_hi - 1: each
+        antenna's gains there become their complex mean (asynchronous; call
+        after `update`)."""
+        B.check(self._lib.epical_average_channels(self.handle, int(c_lo), int(c_hi)))
+
     def sync(self) -> int:
         """Wait for the stream; return the number of gains held since the
         last sync (EPIC_ERR_NUMERIC is reported through the count)."""

@@ -130,6 +130,9 @@ cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
                                     const unsigned char* flags, double2* out, cudaStream_t s);
 cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s);
+// Complex mean of the gains of channels [c_lo, c_hi) per unflagged antenna.
+cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigned char* flags, double2* gain,
+                                    float2* wgain, cudaStream_t s);
 
 // Arguments of one batch of the plain unfused path (epic_unfused.cu).
 struct UnfusedArgs {

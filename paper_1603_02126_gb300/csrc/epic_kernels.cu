@@ -692,6 +692,31 @@ __global__ void set_gains_kernel(int n, const double2* __restrict__ g_in, double
   w[i] = make_float2(static_cast<float>(v.x / m2), static_cast<float>(-v.y / m2));
 }
 
+// Gains constant across channels c_lo .. c_hi - 1 (Sec. 4): per unflagged
+// antenna, the complex mean of those channels' gains replaces each of them
+// (FP64; a zero or non-finite mean leaves the antenna unchanged).
+__global__ void average_channels_kernel(int n_ant, int c_lo, int c_hi, const unsigned char* __restrict__ flags,
+                                        double2* __restrict__ gain, float2* __restrict__ wgain) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_ant || flags[a]) return;
+  double sr = 0.0, si = 0.0;
+  for (int c = c_lo; c < c_hi; ++c) {
+    const double2 g = gain[static_cast<size_t>(c) * n_ant + a];
+    sr += g.x;
+    si += g.y;
+  }
+  const double inv = 1.0 / static_cast<double>(c_hi - c_lo);
+  sr *= inv;
+  si *= inv;
+  const double m2 = sr * sr + si * si;
+  if (!(m2 > 0.0) || !isfinite(m2)) return;
+  const float2 w = make_float2(static_cast<float>(sr / m2), static_cast<float>(-si / m2));
+  for (int c = c_lo; c < c_hi; ++c) {
+    gain[static_cast<size_t>(c) * n_ant + a] = make_double2(sr, si);
+    wgain[static_cast<size_t>(c) * n_ant + a] = w;
+  }
+}
+
 // EPICal update (Eqs. 15-17) in FP64, one thread per (channel, antenna).
 __global__ void epical_update_kernel(const UpdateArgs A) {
   const int n = A.n_chan * A.n_ant;
@@ -834,6 +859,12 @@ cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, 
                                     const unsigned char* flags, double2* out, cudaStream_t s) {
   const int n = n_chan * n_ant;
   adjoint_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, n_ant, dldw, gain, flags, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigned char* flags, double2* gain,
+                                    float2* wgain, cudaStream_t s) {
+  average_channels_kernel<<<(n_ant + 255) / 256, 256, 0, s>>>(n_ant, c_lo, c_hi, flags, gain, wgain);
   return cudaGetLastError();
 }
 

@@ -1161,6 +1161,15 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   return EPIC_OK;
 }
 
+epic_status epical_average_channels(epic_plan_t p, int c_lo, int c_hi) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!(0 <= c_lo && c_lo < c_hi && c_hi <= p->nc))
+    return fail(EPIC_ERR_INVALID_ARG, "channel band must satisfy 0 <= c_lo < c_hi <= C");
+  EPIC_CUDA(epic::launch_average_channels(p->na, c_lo, c_hi, p->d_flags.p, p->d_gain.p, p->d_wgain.p,
+                                          p->stream));
+  return EPIC_OK;
+}
+
 epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
   if (epic_status s = check_plan(p)) return s;
   if (!p->cal) return fail(EPIC_ERR_STATE, "EPICal is not configured");

@@ -96,4 +96,5 @@ def test_create_rejects_on_host(lib, over, code):
 def test_null_plan_calls_fail_cleanly(lib):
     assert lib.epic_image(None, None, 1, None, 0) == 1
     assert lib.epical_update(None, None, None) == 1
+    assert lib.epical_average_channels(None, 0, 1) == 1
     assert lib.epic_plan_destroy(None) == 0

@@ -219,6 +219,39 @@ def test_epical_noise_free_converges_on_gpu():
     assert np.max(np.abs(ga - g_true[0]) / np.abs(g_true[0])) < 1e-4
 
 
+def test_epical_channel_average_loop_matches_oracle():
+    """Gains taken as constant across channels 1..4 of six (Sec. 4): six
+    feedback loops, each followed by the channel average, match the oracle's
+    loop step for step; the averaged channels end with one gain per antenna
+    and the others keep their own."""
+    from paper_1603_02126_gb300 import Plan
+    rng = np.random.default_rng(41)
+    Na, C = 24, 6
+    ant = synth.layout_disc(Na, 20.0, rng, 1.0)
+    f = np.linspace(49e6, 52e6, C)
+    g = np.repeat(synth.true_gains(1, Na, rng), C, axis=0)
+    sky = np.array([[0.0, 0.0, 4.0], [0.2, -0.1, 1.0]])
+    flags = np.zeros(Na, bool)
+    flags[5] = True
+    p = Plan(ant, f, 32, 0.5, input="c64", flags=flags)
+    p.configure((0.0, 0.0), sky, 0.5)
+    oplan = O.Plan(ant, f, 32, 0.5, model_lmS=sky, flags=flags)
+    gref = np.ones((C, Na), complex)
+    rr = np.random.default_rng(5)
+    for _ in range(6):
+        E = synth.voltages(ant, f, g, sky, 300, 1.0, rr).astype(np.complex64)
+        p.image(torch.from_numpy(E).cuda())
+        p.update()
+        p.average_channels(1, 5)
+        gref, *_ = O.epical_interval(oplan, E.astype(np.complex128), gref, 0.5, with_image=False)
+        gref = O.average_channels(gref, 1, 5, flags)
+    gg = p.gains()
+    live = ~flags
+    amp, ph = _gain_err(gg[:, live], gref[:, live])
+    assert amp <= GAIN_TOL and ph <= GAIN_TOL, (amp, ph)
+    assert np.array_equal(gg[1:5], np.repeat(gg[1:2], 4, axis=0))
+    assert not np.allclose(gg[0, live], gg[1, live])
+
 def test_epical_held_antennas_and_state_roundtrip():
     w, b, Eint = _lwa_small(1, 32, n_ant=64)
     flags = np.zeros(64, bool)
