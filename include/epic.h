@@ -86,6 +86,8 @@ typedef struct {
   void* cuda_stream;           /* cudaStream_t for all work; NULL = default */
   int path;                    /* epic_path */
   size_t workspace_bytes;      /* UNFUSED batch scratch budget; 0 = 2 GiB */
+  const double* kernel_param_ant;  /* host [Na]: kernel_param per antenna (heterogeneous
+                                      illumination patterns), or NULL = kernel_param for all */
 } epic_plan_desc;
 
 /* Read-only facts about a plan (epic_plan_get_info). */

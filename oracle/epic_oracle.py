@@ -78,7 +78,8 @@ def grid_table(ant_xy_m, freq_hz, grid_n: int, cell: float,
     floor(p + 0.5); taps are base + d with d in [-(K-1)/2, (K-1)/2] per axis.
     Gaussian: W = exp(-|j - p|^2 / (2 sigma^2)), sigma = param cells.
     Tophat: W = 1 for taps inside a square of side `param` metres centred on
-    the antenna, else 0.  Weights are normalised to sum to 1 so that the far
+    the antenna, else 0.  `param` may also be an array [Na], one value per
+    antenna (heterogeneous illumination patterns).  Weights are normalised to sum to 1 so that the far
     field pattern is 1 at its centre (Sec. 2.1, normalisation of W_a).
     Flagged antennas get zero weights (excluded from the image).
 
@@ -94,6 +95,7 @@ def grid_table(ant_xy_m, freq_hz, grid_n: int, cell: float,
         raise ValueError("kernel support must be odd")
     h = (K - 1) // 2
     flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
+    pa = np.broadcast_to(np.asarray(param, np.float64), (Na,))
     base = np.zeros((C, Na, 2), np.int64)
     W = np.zeros((C, Na, K, K), np.float64)
     for c in range(C):
@@ -112,9 +114,9 @@ def grid_table(ant_xy_m, freq_hz, grid_n: int, cell: float,
                     jy = b[1] + dy - h
                     if kernel == "gaussian":
                         d2 = (jx - p[0]) ** 2 + (jy - p[1]) ** 2
-                        W[c, a, dy, dx] = np.exp(-d2 / (2.0 * param * param))
+                        W[c, a, dy, dx] = np.exp(-d2 / (2.0 * pa[a] * pa[a]))
                     elif kernel == "tophat":
-                        half = (param * freqs[c] / C_LIGHT) / cell / 2.0
+                        half = (pa[a] * freqs[c] / C_LIGHT) / cell / 2.0
                         inside = abs(jx - p[0]) <= half and abs(jy - p[1]) <= half
                         W[c, a, dy, dx] = 1.0 if inside else 0.0
                     else:
@@ -360,6 +362,7 @@ def epical_interval(plan: Plan, E: np.ndarray, g: np.ndarray, gamma: float,
     correlate each raw antenna signal with the calibrator pixel and apply
     the damped update.  Returns (g^{(n+1)}, K, P, image or None, held)."""
     T, C, Na = E.shape
+    g = np.asarray(g, np.complex128)       # gains are complex (Eqs. 15-17)
     if with_image:
         img, pix = image_interval(plan, E, g)
     else:

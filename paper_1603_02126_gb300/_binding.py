@@ -49,6 +49,7 @@ class PlanDesc(ct.Structure):
         ("cuda_stream", ct.c_void_p),
         ("path", ct.c_int),
         ("workspace_bytes", ct.c_size_t),
+        ("kernel_param_ant", c_dp),
     ]
 
 

@@ -79,7 +79,14 @@ class Plan:
         d.cell_wavelengths = float(cell)
         d.kernel = _KERNELS[kernel]
         d.kernel_support = int(support)
-        d.kernel_param = float(param)
+        kp = np.asarray(param, np.float64)
+        if kp.ndim == 0:
+            d.kernel_param = float(kp)
+            self._kp = None
+        else:                                   # one kernel parameter per antenna
+            self._kp = np.ascontiguousarray(kp.reshape(-1))
+            d.kernel_param = float(self._kp[0]) if self._kp.size else 0.0
+            d.kernel_param_ant = self._kp.ctypes.data_as(B.c_dp)
         d.input = _INPUTS[input]
         d.voltage_scale = None if self._vs is None else self._vs.ctypes.data_as(B.c_fp)
         d.flags = None if self._fl is None else self._fl.ctypes.data_as(B.c_u8p)

@@ -66,6 +66,7 @@ struct epic_plan_s {
   // description
   int na = 0, nc = 0, n = 0, k = 0, input = 0, kernel = 0;
   double cell = 0.5, kparam = 0.5;
+  std::vector<double> kparam_ant;   // per-antenna kernel parameter (empty: kparam for all)
   std::vector<double> ant;      // [Na][2]
   std::vector<double> freq;     // [C]
   std::vector<float> vscale;    // [C]
@@ -460,6 +461,10 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     return fail(EPIC_ERR_INVALID_ARG, "unknown kernel type");
   if (!(d->kernel_param > 0) || !std::isfinite(d->kernel_param))
     return fail(EPIC_ERR_INVALID_ARG, "kernel_param must be > 0");
+  if (d->kernel_param_ant)
+    for (int a = 0; a < d->n_ant; ++a)
+      if (!(d->kernel_param_ant[a] > 0) || !std::isfinite(d->kernel_param_ant[a]))
+        return fail(EPIC_ERR_INVALID_ARG, "kernel_param_ant must be > 0 for every antenna");
   if (d->input != EPIC_IN_CI4 && d->input != EPIC_IN_COMPLEX64)
     return fail(EPIC_ERR_INVALID_ARG, "unknown input format");
   if (d->precision != EPIC_PREC_FP32 && d->precision != EPIC_PREC_FP16 && d->precision != EPIC_PREC_BF16)
@@ -500,6 +505,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   p->k = d->kernel_support;
   p->kernel = d->kernel;
   p->kparam = d->kernel_param;
+  if (d->kernel_param_ant) p->kparam_ant.assign(d->kernel_param_ant, d->kernel_param_ant + d->n_ant);
   p->cell = d->cell_wavelengths;
   p->input = d->input;
   p->ant.assign(d->ant_xy_m, d->ant_xy_m + 2 * d->n_ant);
@@ -556,7 +562,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       }
       double* w = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
       double sum = 0.0;
-      const double half = (p->kparam * f / kC) / p->cell / 2.0;
+      const double kp = p->kparam_ant.empty() ? p->kparam : p->kparam_ant[a];
+      const double half = (kp * f / kC) / p->cell / 2.0;
       for (int dy = 0; dy < K; ++dy)
         for (int dx = 0; dx < K; ++dx) {
           const int jx = bx + dx - h, jy = by + dy - h;
@@ -564,7 +571,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
           if (p->kernel == EPIC_KERNEL_GAUSSIAN) {
             const double ex = jx - px, ey = jy - py;
             const double d2 = ex * ex + ey * ey;
-            v = std::exp(-d2 / (2.0 * p->kparam * p->kparam));
+            v = std::exp(-d2 / (2.0 * kp * kp));
           } else {
             v = (std::fabs(jx - px) <= half && std::fabs(jy - py) <= half) ? 1.0 : 0.0;
           }

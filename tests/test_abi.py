@@ -61,6 +61,10 @@ def _desc(B, **over):
             keep["ant2"] = a
             d.ant_xy_m = a.ctypes.data_as(B.c_dp)
             d.n_ant = a.shape[0]
+        elif k == "kernel_param_ant":
+            a = np.ascontiguousarray(v, np.float64)
+            keep["kpa"] = a
+            d.kernel_param_ant = a.ctypes.data_as(B.c_dp)
         else:
             setattr(d, k, v)
     return d, keep
@@ -78,6 +82,7 @@ def _desc(B, **over):
     (dict(grid_n=1024), 7),
     (dict(ant=[[60.0, 0.0], [0.0, 0.0]]), 2),
     (dict(path=5), 1),                      # unknown path
+    (dict(kernel_param_ant=[0.5, -1.0, 0.5]), 1),   # per-antenna parameters must be > 0
     (dict(path=4, grid_n=32), 7),           # warp-specialised form: N = 64 or 128 only
     (dict(path=4, precision=2), 7),         # ... and FP32 only
     (dict(path=3, grid_n=128), 7),          # cluster form: N = 256 or 512 only

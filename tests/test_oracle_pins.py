@@ -465,3 +465,27 @@ def test_channel_averaging_reduces_gain_noise():
                 gc = O.average_channels(gc, 0, C)
         err[avg] = np.mean([O.gain_error(O.align_phase(gc[c], g1[0]), g1[0]) for c in range(C)])
     assert err[True] < 0.7 * err[False], err
+
+
+# --------------------------------------------------------------------------
+# heterogeneous illumination patterns (one kernel parameter per antenna)
+# --------------------------------------------------------------------------
+def test_grid_table_per_antenna_parameters():
+    """A per-antenna parameter array equal to the scalar gives the scalar's
+    table; with different values, each antenna's stencil is the one it gets
+    alone with its own value (antennas do not interact in Eq. 9's weights);
+    a wider Gaussian puts less weight on the nearest cell."""
+    rng = np.random.default_rng(17)
+    ant = rng.uniform(-8, 8, size=(12, 2))
+    freqs = [45e6, 70e6]
+    b0, W0 = O.grid_table(ant, freqs, 64, 0.5, "gaussian", 5, 0.6)
+    b1, W1 = O.grid_table(ant, freqs, 64, 0.5, "gaussian", 5, np.full(12, 0.6))
+    assert np.array_equal(b0, b1) and np.array_equal(W0, W1)
+    sig = rng.uniform(0.3, 1.2, 12)
+    b2, W2 = O.grid_table(ant, freqs, 64, 0.5, "gaussian", 5, sig)
+    for a in range(12):
+        ba, Wa = O.grid_table(ant[a:a + 1], freqs, 64, 0.5, "gaussian", 5, sig[a])
+        assert np.array_equal(b2[:, a], ba[:, 0]) and np.array_equal(W2[:, a], Wa[:, 0])
+    narrow, wide = np.argmin(sig), np.argmax(sig)
+    for c in range(2):
+        assert W2[c, narrow, 2, 2] > W2[c, wide, 2, 2]
