@@ -103,3 +103,33 @@ def test_null_plan_calls_fail_cleanly(lib):
     assert lib.epical_update(None, None, None) == 1
     assert lib.epical_average_channels(None, 0, 1) == 1
     assert lib.epic_plan_destroy(None) == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the descriptor, info and tune-result structs
+    have the sizes and field offsets a C compiler gives include/epic.h."""
+    import shutil
+    import subprocess
+    from paper_1603_02126_gb300 import _binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"epic_plan_desc": B.PlanDesc, "epic_plan_info": B.PlanInfo,
+               "epic_tune_result": B.TuneResult}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "epic.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
