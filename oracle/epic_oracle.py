@@ -17,7 +17,9 @@ closed form, source position), the EPICal correlation and update (visibility
 route, zenith single-source limit, noise-free fixed point, damping closed
 form, effective integration time), the visibility solve (noise-free
 truth) and the chi^2 model image and gradient (noise-free identity, central
-finite differences).  Nothing in this module is parity-unpinned.
+finite differences), and the sampled-output checkers image_pixels and
+correlate_sampled (visibility route at every pixel, the full transform).
+Nothing in this module is parity-unpinned.
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ C_LIGHT = 299792458.0  # speed of light, m/s
 __all__ = [
     "C_LIGHT", "GridTooSmall", "unpack_ci4", "antenna_uv", "grid_table",
     "apply_gains", "grid_frames", "efield_image", "efield_image_direct",
-    "dirty_image", "calibrator_pixel", "pixel_row", "model_visibilities",
+    "calibrator_pixel", "pixel_row", "model_visibilities",
     "cal_denominator", "correlate", "epical_update", "image_interval",
     "epical_interval", "visibilities", "visibility_solve", "gain_error",
     "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
@@ -191,12 +193,6 @@ def efield_image_direct(G: np.ndarray, n_ant: int) -> np.ndarray:
                     acc += G[jy, jx] * np.exp(2j * np.pi * m / n)
             out[ky, kx] = acc / n_ant
     return out
-
-
-def dirty_image(Eimg: np.ndarray) -> np.ndarray:
-    """I'(s_k) = < |E'(s_k, t)|^2 >_t (Sec. 2.1: squared and averaged in
-    time).  Eimg: [T, N, N]."""
-    return np.mean(np.abs(Eimg) ** 2, axis=0)
 
 
 # --------------------------------------------------------------------------

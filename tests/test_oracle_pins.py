@@ -201,6 +201,82 @@ def test_image_equals_gridded_visibilities_with_autos():
         assert np.max(np.abs(img[c] - ref)) <= 1e-12 * np.max(ref)
 
 
+def _offcentre_case(rng, Na=7, N=16, T=45, K=5):
+    """Small off-centre case with a flagged antenna, support K and a calibrator
+    away from the phase centre (shared by the sampled-checker pins)."""
+    ant = synth.layout_disc(Na, 6.0, rng, 1.0)
+    f = [47e6, 66e6]
+    g = synth.true_gains(2, Na, rng)
+    sky = np.array([[0.19, -0.31, 3.0], [-0.27, 0.12, 1.5]])
+    E = synth.voltages(ant, f, g, sky, T, 1.0, rng)
+    flags = np.zeros(Na, bool)
+    flags[3] = True
+    cal = (0.25, -0.375)                      # pixel (12, 5) at N = 16, du = 0.5
+    plan = O.Plan(ant, f, N, 0.5, support=K, param=0.8, flags=flags, cal_lm=cal,
+                  model_lmS=sky)
+    return plan, E, synth.true_gains(2, Na, rng)
+
+
+def test_image_pixels_equal_visibility_route_every_pixel():
+    """image_pixels, the checker of every full-size image test, at all N^2
+    pixels of a small case (two channels, flags, K = 5, T not a multiple of
+    the block) equals the Sec. 2.1 statement I_k = sum_ab A_ka conj(A_kb) V'_ab
+    with explicit A, and the full-transform image_interval.  A swapped axis
+    or a wrong centring offset in its single-pixel DFT fails here."""
+    rng = np.random.default_rng(31)
+    plan, E, gcur = _offcentre_case(rng)
+    N = plan.N
+    T = E.shape[0]
+    pix = [(kx, ky) for ky in range(N) for kx in range(N)]
+    full, _ = O.image_interval(plan, E, gcur)
+    for c in range(2):
+        got = O.image_pixels(plan, E, gcur, c, pix, block=16).reshape(N, N)
+        A = _explicit_A(plan, c)
+        Ec = E[:, c, :] / gcur[c]
+        V = Ec.T @ np.conj(Ec) / T
+        ref = np.einsum("yxa,ab,yxb->yx", A, V, np.conj(A)).real
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(ref)
+        assert np.max(np.abs(got - full[c])) <= 1e-12 * np.max(full[c])
+    # a non-square pixel list keeps (kx, ky) order: (kx, ky) != (ky, kx)
+    got = O.image_pixels(plan, E, gcur, 1, [(3, 11), (11, 3)])
+    assert np.allclose(got, [full[1][11, 3], full[1][3, 11]], rtol=1e-12, atol=0)
+
+
+def test_correlate_sampled_equals_visibility_route():
+    """correlate_sampled (K_a, P_a of selected antennas with the calibrator
+    pixel from the single-pixel sum) gives C_a of Eq. 15 equal to the
+    visibility route sum_{b != a} conj(A_{0,b}) V_ab / conj(g_b), and K, P
+    equal to correlate() on image_interval's pixel series."""
+    rng = np.random.default_rng(32)
+    plan, E, gcur = _offcentre_case(rng)
+    Na = plan.Na
+    ants = [6, 0, 3, 4]
+    _, pixser = O.image_interval(plan, E, gcur)
+    for c in range(2):
+        Kc, P = O.correlate_sampled(plan, E, gcur, c, ants, block=13)
+        Kf, Pf = O.correlate(E[:, c, :], pixser[:, c])
+        assert np.allclose(Kc, Kf[ants], rtol=1e-12, atol=1e-14)
+        assert np.allclose(P, Pf[ants], rtol=1e-12, atol=0)
+        V = O.visibilities(E[:, c, :])
+        for i, a in enumerate(ants):
+            Ca = Kc[i] - np.conj(plan.A0[c, a]) * P[i] / np.conj(gcur[c, a])
+            ref = sum(np.conj(plan.A0[c, b]) * V[a, b] / np.conj(gcur[c, b])
+                      for b in range(Na) if b != a and not plan.flags[b])
+            assert abs(Ca - ref) <= 1e-12 * abs(ref), (c, a)
+
+
+def test_epical_interval_pixel_only_equals_full_image_route():
+    """epical_interval's single-pixel branch (no image) gives the same gains
+    and sums as the branch through the full image."""
+    rng = np.random.default_rng(33)
+    plan, E, gcur = _offcentre_case(rng)
+    a = O.epical_interval(plan, E, gcur, 0.4, with_image=True)
+    b = O.epical_interval(plan, E, gcur, 0.4, with_image=False)
+    for x, y in zip((a[0], a[1], a[2]), (b[0], b[1], b[2])):
+        assert np.allclose(x, y, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(a[4], b[4])
+
+
 # --------------------------------------------------------------------------
 # EPICal (Eqs. 12-17)
 # --------------------------------------------------------------------------
