@@ -10,7 +10,7 @@ Data model (the paper's measurement equation, used only to make test data):
   E_a(f,t) = g_a(f) * sum_s sqrt(S_s) z_s(t) exp(-2 pi i u_a . s_s) + n_a(t)
 with u_a = r_a f / c in wavelengths (Sec. 2.1, Eq. 3 propagation and Eq. 7
 gain/noise corruption).  Source signals z_s are complex Gaussian with unit
-variance (Sec. 4: the source amplitudes vary randomly in time) or, for the
+variance (Sec. 3: the source amplitudes vary randomly in time) or, for the
 noise-free convergence pins, unit-modulus phasors.
 
 4-bit complex input format: one byte per (t, c, a); the high nibble holds the

@@ -82,7 +82,8 @@ typedef struct {
   int input;                   /* epic_input_format of the voltages */
   const float* voltage_scale;  /* host [C] multiplier per channel, or NULL = 1 */
   const unsigned char* flags;  /* host [Na], 1 = antenna flagged, or NULL */
-  int precision;               /* epic_precision of the FFT; FP32 only here */
+  int precision;               /* epic_precision of the FFT: FP32, or FP16 / BF16
+                                  (column DFT on tensor cores, UNFUSED/AUTO path) */
   void* cuda_stream;           /* cudaStream_t for all work; NULL = default */
   int path;                    /* epic_path */
   size_t workspace_bytes;      /* UNFUSED batch scratch budget; 0 = 2 GiB */
@@ -168,12 +169,15 @@ epic_status epic_image_host(epic_plan_t plan, const void* h_volt, long long n_ti
  * holds until exit; T is processed in chunks that fit beside the image.
  * Arguments and result as epic_image_host.  The image [C][N][N] float64 plus
  * one time sample of voltages must fit in 32 MiB, else INVALID_ARG with a
- * message; a plan on the UNFUSED path gives UNSUPPORTED (that path needs its
- * own scratch).  The first call on a device looks up the array's device address
- * (make that first call before any stream capture).  All calls share the
- * array: calls whose GPU work overlaps (several host threads or plans on
- * different streams) race and must be serialised by the caller.
- * Synchronous. */
+ * message.  The call needs a plan on the fused FP32 path (EPIC_PATH_FUSED,
+ * what AUTO picks for N <= 128 at FP32); every other path (UNFUSED, CLUSTER,
+ * PIPED, FP16/BF16) needs plan scratch and gives UNSUPPORTED before the array
+ * is touched.  The first call on a device looks up the array's device address
+ * (make that first call before any stream capture); the address is kept for
+ * the life of the device's context, so do not call this entry point on a
+ * device after cudaDeviceReset.  All calls share the array: calls whose GPU
+ * work overlaps (several host threads or plans on different streams) race
+ * and must be serialised by the caller.  Synchronous. */
 epic_status epic_image_host_static(epic_plan_t plan, const void* h_volt, long long n_time,
                                    double* h_image, int accumulate);
 
@@ -225,7 +229,7 @@ epic_status epical_configure(epic_plan_t plan, double cal_l, double cal_m,
  * Errors: STATE (not configured, or no frames since the last update). */
 epic_status epical_update(epic_plan_t plan, double* d_gains_out, int* d_status);
 
-/* Gains taken as constant across a band of channels (Sec. 4: the LWA
+/* Gains taken as constant across a band of channels (Sec. 5: the LWA
  * demonstration averages the per-channel solutions across its central
  * channels to raise the signal to noise).  For every unflagged antenna the
  * gains of channels c_lo <= c < c_hi are replaced by their plain complex

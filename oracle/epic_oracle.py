@@ -286,7 +286,7 @@ def epical_update(Kc, P, A0, D, g, gamma: float, flags=None, d_min: float = 0.0)
 
 
 def average_channels(g, c_lo: int, c_hi: int, flags=None):
-    """Gains assumed constant across a band of channels (Sec. 4, LWA data):
+    """Gains assumed constant across a band of channels (Sec. 5, LWA data):
     after an interval's update, every channel c_lo <= c < c_hi takes the
     plain mean of the complex solutions of those channels, antenna by
     antenna.  Channels outside the band, flagged antennas and antennas whose

@@ -144,47 +144,57 @@ class Plan:
                                      _dptr(image, torch.float64, "image"), int(bool(accumulate))))
         return image
 
-    def image_host(self, volt, image=None, accumulate=False):
-        """Host-buffer form (copies inside the call).  volt: numpy array or
-        CPU tensor [T][C][Na]; returns a float64 [C][N][N] numpy image."""
+    def _host_buffers(self, volt, image, name):
+        """Validated host pointers of a [T][C][Na] voltage array and a
+        [C][N][N] float64 image (allocated if None): the C side copies
+        exactly those sizes, so a mismatched array is refused here."""
         torch = _torch()
+        want = np.uint8 if self.input == "ci4" else np.complex64
         if isinstance(volt, torch.Tensor):
             if volt.is_cuda:
-                raise TypeError("image_host takes host memory")
+                raise TypeError(f"{name} takes host memory")
+            tdt = torch.uint8 if self.input == "ci4" else torch.complex64
+            if volt.dtype != tdt:
+                raise TypeError(f"volt must be {tdt}, got {volt.dtype}")
             vt = volt.contiguous()
-            vptr = ct.c_void_p(vt.data_ptr())
-            T = vt.shape[0]
+            vptr, vshape = ct.c_void_p(vt.data_ptr()), tuple(vt.shape)
         else:
+            if np.asarray(volt).dtype != want:
+                raise TypeError(f"volt must be {np.dtype(want)}, got {np.asarray(volt).dtype}")
             vt = np.ascontiguousarray(volt)
-            vptr = ct.c_void_p(vt.ctypes.data)
-            T = vt.shape[0]
+            vptr, vshape = ct.c_void_p(vt.ctypes.data), vt.shape
+        if len(vshape) != 3 or vshape[1:] != (self.n_chan, self.n_ant) or vshape[0] < 1:
+            raise ValueError(f"volt must be [T][{self.n_chan}][{self.n_ant}], got {list(vshape)}")
+        shape = (self.n_chan, self.grid_n, self.grid_n)
         if image is None:
-            image = np.zeros((self.n_chan, self.grid_n, self.grid_n), np.float64)
+            image = np.zeros(shape, np.float64)
         if isinstance(image, torch.Tensor):
+            if image.is_cuda or image.dtype != torch.float64 or tuple(image.shape) != shape \
+                    or not image.is_contiguous():
+                raise ValueError(f"image must be a contiguous host float64 {list(shape)} array")
             iptr = ct.c_void_p(image.data_ptr())
         else:
+            if not isinstance(image, np.ndarray) or image.dtype != np.float64 or image.shape != shape \
+                    or not image.flags.c_contiguous:
+                raise ValueError(f"image must be a C-contiguous float64 {list(shape)} array")
             iptr = ct.c_void_p(image.ctypes.data)
-        B.check(self._lib.epic_image_host(self.handle, vptr, int(T), iptr, int(bool(accumulate))))
+        return vt, vptr, int(vshape[0]), image, iptr
+
+    def image_host(self, volt, image=None, accumulate=False):
+        """Host-buffer form (copies inside the call).  volt: numpy array or
+        CPU tensor [T][C][Na] (uint8 ci4 or complex64); returns the float64
+        [C][N][N] image (a new numpy array if image is None)."""
+        vt, vptr, T, image, iptr = self._host_buffers(volt, image, "image_host")
+        B.check(self._lib.epic_image_host(self.handle, vptr, T, iptr, int(bool(accumulate))))
         return image
 
     def image_host_static(self, volt, image=None, accumulate=False):
         """image_host without any device allocation: stages through the
         library's fixed 32 MiB device array (for callers that may not call
-        cudaMalloc).  Same arguments and result as image_host."""
-        torch = _torch()
-        if isinstance(volt, torch.Tensor):
-            if volt.is_cuda:
-                raise TypeError("image_host_static takes host memory")
-            vt = volt.contiguous()
-            vptr = ct.c_void_p(vt.data_ptr())
-        else:
-            vt = np.ascontiguousarray(volt)
-            vptr = ct.c_void_p(vt.ctypes.data)
-        if image is None:
-            image = np.zeros((self.n_chan, self.grid_n, self.grid_n), np.float64)
-        iptr = ct.c_void_p(image.data_ptr() if isinstance(image, torch.Tensor) else image.ctypes.data)
-        B.check(self._lib.epic_image_host_static(self.handle, vptr, int(vt.shape[0]), iptr,
-                                                 int(bool(accumulate))))
+        cudaMalloc).  Same arguments and result as image_host; the plan must
+        be on the fused FP32 path."""
+        vt, vptr, T, image, iptr = self._host_buffers(volt, image, "image_host_static")
+        B.check(self._lib.epic_image_host_static(self.handle, vptr, T, iptr, int(bool(accumulate))))
         return image
 
     def set_gains_device(self, gains):

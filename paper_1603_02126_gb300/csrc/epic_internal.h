@@ -230,5 +230,6 @@ size_t plan_frame_bytes(const epic_plan_s* p);   // voltages of one time sample,
 size_t plan_image_elems(const epic_plan_s* p);   // C * N * N
 cudaStream_t plan_stream(const epic_plan_s* p);
 int plan_device(const epic_plan_s* p);
+int plan_path(const epic_plan_s* p);            // epic_path in use (never AUTO)
 int set_error(int status, const char* msg);     // records epic_last_error(), returns status
 }  // namespace epic

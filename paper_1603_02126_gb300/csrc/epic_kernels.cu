@@ -692,7 +692,7 @@ __global__ void set_gains_kernel(int n, const double2* __restrict__ g_in, double
   w[i] = make_float2(static_cast<float>(v.x / m2), static_cast<float>(-v.y / m2));
 }
 
-// Gains constant across channels c_lo .. c_hi - 1 (Sec. 4): per unflagged
+// Gains constant across channels c_lo .. c_hi - 1 (Sec. 5): per unflagged
 // antenna, the complex mean of those channels' gains replaces each of them
 // (FP64; a zero or non-finite mean leaves the antenna unchanged).
 __global__ void average_channels_kernel(int n_ant, int c_lo, int c_hi, const unsigned char* __restrict__ flags,

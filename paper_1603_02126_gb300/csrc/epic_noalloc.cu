@@ -31,7 +31,10 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 // Device address of g_static_scratch per device.  The symbol's name is a
 // host-side stand-in in host code, so the address is looked up once per
-// device with that device current.
+// device with that device current.  The cached address belongs to the
+// device's current context: it does not survive cudaDeviceReset (the module
+// is loaded again into the new context and the array may move), so a caller
+// that resets a device must not call this entry point on it afterwards.
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
@@ -69,6 +72,11 @@ extern "C" epic_status epic_image_host_static(epic_plan_t p, const void* h_volt,
   if (dev != epic::plan_device(p))
     return static_cast<epic_status>(
         epic::set_error(EPIC_ERR_INVALID_ARG, "current device is not the plan's device"));
+  // only the fused FP32 kernel images from the array alone; every other path
+  // needs plan scratch.  Refused before anything touches the array.
+  if (epic::plan_path(p) != EPIC_PATH_FUSED)
+    return static_cast<epic_status>(epic::set_error(
+        EPIC_ERR_UNSUPPORTED, "epic_image_host_static needs a plan on the fused FP32 path (EPIC_PATH_FUSED)"));
 
   const size_t img_bytes = epic::plan_image_elems(p) * sizeof(double);
   const size_t img_span = (img_bytes + 255) & ~static_cast<size_t>(255);

@@ -1551,6 +1551,8 @@ cudaStream_t plan_stream(const epic_plan_s* p) { return p->stream; }
 
 int plan_device(const epic_plan_s* p) { return p->device; }
 
+int plan_path(const epic_plan_s* p) { return p->path; }
+
 int set_error(int status, const char* msg) { return fail(static_cast<epic_status>(status), msg); }
 
 }  // namespace epic

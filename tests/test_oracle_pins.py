@@ -492,7 +492,7 @@ def test_chi2_gradient_matches_finite_differences():
 
 
 # --------------------------------------------------------------------------
-# gains constant across a band of channels (Sec. 4, LWA demonstration)
+# gains constant across a band of channels (Sec. 5, LWA demonstration)
 # --------------------------------------------------------------------------
 def test_average_channels_invariants():
     """In-band channels all take one value per antenna whose band sum equals

@@ -66,3 +66,43 @@ def test_static_scratch_rejects_oversized_image():
     with pytest.raises(EpicError) as ei:
         p.image_host_static(v)
     assert "static scratch" in str(ei.value)
+
+
+def test_static_scratch_epical_interval_matches_image_host():
+    """EPICal armed: one interval imaged in two chunks through the static
+    array accumulates the same K_a, P_a and frame count as epic_image_host,
+    so the gain updates agree within the parity bar (1e-4)."""
+    from paper_1603_02126_gb300 import Plan
+    w = synth.workload("lwa", n_time=2500)
+    rng = np.random.default_rng(5)
+    E = synth.voltages(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:60], 2500,
+                       w["noise_power"], rng)
+    b = synth.quantise_ci4(E, w["lsb"])
+    plans = [Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+                  voltage_scale=w["lsb"]) for _ in range(2)]
+    for p in plans:
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+    img_ref = plans[0].image_host(b)
+    img_got = plans[1].image_host_static(b)
+    assert _rel(img_got, img_ref) <= IMG_TOL
+    assert plans[0].info()["frames_pending"] == plans[1].info()["frames_pending"] == 2500
+    for p in plans:
+        p.update()
+        assert p.sync() == 0
+    g_ref, g_got = plans[0].gains(), plans[1].gains()
+    amp = np.max(np.abs(np.abs(g_got) - np.abs(g_ref)) / np.abs(g_ref))
+    ph = np.max(np.abs(np.angle(g_got * np.conj(g_ref))))
+    assert amp <= 1e-4 and ph <= 1e-4, (amp, ph)
+
+
+def test_static_scratch_refuses_non_fused_plan():
+    """A plan on any other path needs its own scratch: UNSUPPORTED, before
+    the size check (this unfused plan's image would also exceed the array)."""
+    from paper_1603_02126_gb300 import EpicError, Plan
+    rng = np.random.default_rng(6)
+    ant = synth.layout_disc(16, 10.0, rng, 1.0)
+    freqs = np.linspace(40e6, 60e6, 260)
+    p = Plan(ant, freqs, 128, 0.5, input="ci4", path="unfused")
+    with pytest.raises(EpicError) as ei:
+        p.image_host_static(np.zeros((2, 260, 16), np.uint8))
+    assert ei.value.status == 7           # EPIC_ERR_UNSUPPORTED
