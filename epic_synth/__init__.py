@@ -137,26 +137,41 @@ def sky_diffuse(n_src: int, total_flux: float, rng: np.random.Generator) -> np.n
 # --------------------------------------------------------------------------
 def voltages(ant_xy_m: np.ndarray, freq_hz: np.ndarray, gains: np.ndarray,
              sky_lmS: np.ndarray, n_time: int, noise_power: float,
-             rng: np.random.Generator, unit_modulus: bool = False) -> np.ndarray:
+             rng: np.random.Generator, unit_modulus: bool = False,
+             tones: bool = False) -> np.ndarray:
     """Channelised antenna voltages, complex128 [T][C][Na].
 
-    gains: [C][Na] complex.  sky_lmS: [Ns][3] rows (l, m, S).  noise_power:
-    <|n_a|^2> per sample (0 = noise free).  unit_modulus: source signals are
-    exp(i theta_t) with theta uniform (so <|z|^2> = 1 exactly per sample).
+    gains: [C][Na] complex, or [C][Na][Ns] for gains that differ by source
+    direction.  sky_lmS: [Ns][3] rows (l, m, S).  noise_power: <|n_a|^2> per
+    sample (0 = noise free).  unit_modulus: source signals are exp(i theta_t)
+    with theta uniform (so <|z|^2> = 1 exactly per sample).  tones: source s
+    is the unit-modulus tone exp(2 pi i (k_s t / T + phi_s)) with distinct
+    integers k_s, so that different sources are exactly uncorrelated over
+    the T samples (noise-free sample visibilities equal the model).
     """
     ant = np.asarray(ant_xy_m, float)
     T, C, Na, Ns = n_time, len(freq_hz), ant.shape[0], sky_lmS.shape[0]
     out = np.empty((T, C, Na), np.complex128)
     amp = np.sqrt(sky_lmS[:, 2])
+    gains = np.asarray(gains)
     for c, f in enumerate(freq_hz):
         u = ant * f / C_LIGHT                                   # [Na][2]
         ph = np.exp(-2j * np.pi * (u @ sky_lmS[:, :2].T))      # [Na][Ns]
-        if unit_modulus:
+        if tones:
+            if Ns >= T:
+                raise ValueError("tones need fewer sources than samples")
+            k = rng.choice(np.arange(1, T), size=Ns, replace=False)
+            phi = rng.uniform(0.0, 1.0, size=Ns)
+            z = np.exp(2j * np.pi * (np.outer(np.arange(T), k) / T + phi[None, :]))
+        elif unit_modulus:
             z = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(T, Ns)))
         else:
             z = (rng.normal(size=(T, Ns)) + 1j * rng.normal(size=(T, Ns))) / np.sqrt(2)
-        e = (z * amp) @ ph.T                                    # [T][Na]
-        e = e * gains[c][None, :]
+        if gains.ndim == 3:                                     # direction-dependent
+            e = (z * amp) @ (ph * gains[c]).T
+        else:
+            e = (z * amp) @ ph.T                                # [T][Na]
+            e = e * gains[c][None, :]
         if noise_power > 0:
             e = e + np.sqrt(noise_power / 2) * (rng.normal(size=(T, Na))
                                                 + 1j * rng.normal(size=(T, Na)))

@@ -286,6 +286,18 @@ epic_status epic_plan_get_grid_table(epic_plan_t plan, int* base_xy, double* w);
 epic_status epic_unpack_ci4(epic_plan_t plan, const unsigned char* d_in, float* d_out,
                             long long n);
 
+/* Measurement aid (no counterpart in the paper): launch a grid of `blocks`
+ * CTAs of 256 threads, each thread running 8 independent chains of
+ * 16 * iters fused multiply-adds in FP32 (fp64 = 0) or FP64 (fp64 != 0), on
+ * cuda_stream (cudaStream_t, NULL = default).  *flops receives the FLOP
+ * count of the launch (2 per multiply-add), so that a caller timing the
+ * launch with CUDA events obtains the device's FMA rate: the roofline
+ * denominator of the FP32-arithmetic-bound imaging kernels.  d_sink: device
+ * buffer of at least `blocks` floats (doubles for FP64), never written for
+ * these arguments.  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+epic_status epic_measure_fma_peak(int fp64, int blocks, long long iters, void* d_sink,
+                                  void* cuda_stream, double* flops);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* epic_last_error(void);
 

@@ -35,6 +35,8 @@ __all__ = [
     "epical_interval", "visibilities", "visibility_solve", "gain_error",
     "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
     "model_image", "chi2_loss", "chi2_gradient", "average_channels",
+    "MultiPixelPlan", "pixel_taps", "correlate_multi", "multipixel_update",
+    "direction_update", "multipixel_interval",
 ]
 
 
@@ -420,6 +422,119 @@ def correlate_sampled(plan: Plan, E: np.ndarray, g: np.ndarray, c: int, ants,
         pix[t0:t0 + block] = np.einsum("tyx,y,x->t", G, fy, fx) / plan.norm
     Kc, P = correlate(E[:, c, list(ants)], pix)
     return Kc, P
+
+
+# --------------------------------------------------------------------------
+# multiple-pixel and direction-dependent EPICal (Sec. 6, "Multiple pixel
+# correlations")
+# --------------------------------------------------------------------------
+class MultiPixelPlan(Plan):
+    """EPICal with several calibration pixels (Sec. 6): every raw antenna
+    signal is correlated with the E-field at P image pixels, O(Na P) per
+    sample.  Per channel and pixel p: A_{p,a}, the exact response of pixel
+    k_p to antenna a (as pixel_row), and D_{p,a} = sum_{b != a}
+    conj(A_{p,b}) V^M_ab (as cal_denominator).  pix_lm: [P][2] directions
+    (l, m); each maps to its nearest pixel centre as the calibrator does."""
+
+    def __init__(self, ant_xy_m, freq_hz, grid_n, cell, pix_lm, model_lmS, **kw):
+        super().__init__(ant_xy_m, freq_hz, grid_n, cell, model_lmS=model_lmS, **kw)
+        self.pix = [calibrator_pixel(l, m, self.N, self.cell)
+                    for l, m in np.asarray(pix_lm, np.float64).reshape(-1, 2)]
+        C = len(self.freqs)
+        self.Ap = np.stack([np.stack([pixel_row(self.base[c], self.W[c], self.N, k, self.norm)
+                                      for k in self.pix]) for c in range(C)])      # [C][P][Na]
+        self.Dp = np.stack([np.stack([cal_denominator(self.Ap[c, i],
+                                                      model_visibilities(self.ant, f, model_lmS),
+                                                      self.flags)
+                                      for i in range(len(self.pix))])
+                            for c, f in enumerate(self.freqs)])                   # [C][P][Na]
+
+
+def pixel_taps(plan: Plan, Ecal: np.ndarray, c: int, pixels) -> np.ndarray:
+    """E'(s_k, t) of Eq. 10 at the listed pixels only, for the gain-corrected
+    voltages Ecal [T][Na] of channel c: grid (Eq. 9), then the single-pixel
+    DFT at each k.  Returns [T][P]."""
+    n = plan.N
+    j = np.arange(n) - n // 2
+    G = grid_frames(Ecal, plan.base[c], plan.W[c], n, plan.flags)
+    out = np.zeros((Ecal.shape[0], len(pixels)), np.complex128)
+    for i, (kx, ky) in enumerate(pixels):
+        fx = np.exp(2j * np.pi * np.mod(j * (kx - n // 2), n) / n)
+        fy = np.exp(2j * np.pi * np.mod(j * (ky - n // 2), n) / n)
+        out[:, i] = np.einsum("tyx,y,x->t", G, fy, fx) / plan.norm
+    return out
+
+
+def correlate_multi(E: np.ndarray, taps: np.ndarray):
+    """Eq. 12 for every calibration pixel: K_{a,p} = < E_a(t) conj(E'(s_p, t)) >_t
+    with the uncalibrated voltages, and P_a = < |E_a|^2 >_t (Eq. 15).
+    E: [T][Na], taps: [T][P].  Returns K [Na][P], P [Na]."""
+    T = E.shape[0]
+    Kc = (E.T @ np.conj(taps)) / T
+    P = (np.abs(E) ** 2).sum(axis=0) / T
+    return Kc, P
+
+
+def multipixel_update(Kc, P, Ap, Dp, g, gamma: float, flags=None, d_min: float = 0.0):
+    """Gain update from P pixel correlations.  Eq. 15 per pixel,
+    C_{a,p} = K_{a,p} - conj(A_{p,a}) P_a / conj(g_a); the noise-free fixed
+    point C_{a,p} = g_a D_{p,a} holds for every pixel at once (Eqs. 13-16),
+    and the reading here combines them by least squares over the pixels,
+    g_a <- (1 - gamma) sum_p conj(D_{p,a}) C_{a,p} / sum_p |D_{p,a}|^2
+           + gamma g_a                                    (Eq. 17 damping),
+    which is Eq. 16 exactly when P = 1.  Flagged antennas, a denominator
+    sum_p |D_{p,a}|^2 <= d_min^2 and non-finite results hold g_a.
+    Kc [Na][P], P [Na], Ap / Dp [P][Na], g [Na].  Returns (g_new, held, C)."""
+    if not (0.0 <= gamma < 1.0):
+        raise ValueError("gamma must be in [0, 1)")
+    Na = g.shape[0]
+    flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
+    Cc = Kc - (np.conj(Ap) * (P / np.conj(g))[None, :]).T          # [Na][P]
+    num = np.sum(np.conj(Dp).T * Cc, axis=1)
+    den = np.sum(np.abs(Dp) ** 2, axis=0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gn = (1.0 - gamma) * num / den + gamma * g
+    held = flags | ~(den > d_min * d_min) | ~np.isfinite(gn)
+    return np.where(held, g, gn), held, Cc
+
+
+def direction_update(Cc, Dp, gdir, gamma: float, flags=None, d_min: float = 0.0):
+    """Direction-dependent solutions (Sec. 6): each pixel correlation solves
+    for the gains in its own direction independently, g_{a,p} <- (1 - gamma)
+    C_{a,p} / D_{p,a} + gamma g_{a,p} (Eqs. 16, 17 per pixel).  Cc [Na][P]
+    from multipixel_update, Dp [P][Na], gdir [Na][P].  Flagged antennas,
+    |D_{p,a}| <= d_min and non-finite results hold.  Returns (gdir_new, held)."""
+    Na = gdir.shape[0]
+    flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
+    D = Dp.T
+    with np.errstate(divide="ignore", invalid="ignore"):
+        gn = (1.0 - gamma) * Cc / D + gamma * gdir
+    held = flags[:, None] | ~(np.abs(D) > d_min) | ~np.isfinite(gn)
+    return np.where(held, gdir, gn), held
+
+
+def multipixel_interval(plan: MultiPixelPlan, E: np.ndarray, g: np.ndarray, gdir: np.ndarray,
+                        gamma: float, d_min: float = 0.0):
+    """One multiple-pixel EPICal loop: image the interval's calibration
+    pixels with g^{(n)} (Eqs. 8-10), correlate (Eq. 12 per pixel), then the
+    joint update of the imaging gains and the per-direction updates.
+    E [T][C][Na], g [C][Na], gdir [C][Na][P].
+    Returns (g_new, gdir_new, K [C][Na][P], P [C][Na], held [C][Na])."""
+    T, C, Na = E.shape
+    g = np.asarray(g, np.complex128)
+    gdir = np.asarray(gdir, np.complex128)
+    gn = np.empty_like(g)
+    gdn = np.empty_like(gdir)
+    Ks = np.empty(gdir.shape, np.complex128)
+    Ps = np.empty(g.shape)
+    held = np.zeros(g.shape, bool)
+    for c in range(C):
+        taps = pixel_taps(plan, apply_gains(E[:, c, :], g[c]), c, plan.pix)
+        Ks[c], Ps[c] = correlate_multi(E[:, c, :], taps)
+        gn[c], held[c], Cc = multipixel_update(Ks[c], Ps[c], plan.Ap[c], plan.Dp[c], g[c],
+                                               gamma, plan.flags, d_min)
+        gdn[c], _ = direction_update(Cc, plan.Dp[c], gdir[c], gamma, plan.flags, d_min)
+    return gn, gdn, Ks, Ps, held
 
 
 # --------------------------------------------------------------------------

@@ -299,6 +299,34 @@ class Plan:
 
 
 # C-ABI-named module functions (thin aliases of the Plan methods)
+def measure_fma_peak(fp64=False, stream=None, reps=5):
+    """Measured FMA rate of the device in TFLOP/s (FP32, or FP64): the
+    median over reps of one epic_measure_fma_peak launch timed with CUDA
+    events on `stream` (default: a new stream on the current device).  The
+    roofline denominator of the FP32-arithmetic-bound imaging kernels."""
+    torch = _torch()
+    lib = B.load()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8                       # 8 x 256 threads per SM: 64 warps
+    iters = 64 if fp64 else 4096
+    st = stream if stream is not None else torch.cuda.Stream()
+    sink = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    flops = ct.c_double()
+    times = []
+    for i in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        B.check(lib.epic_measure_fma_peak(int(bool(fp64)), blocks, iters, ct.c_void_p(sink.data_ptr()),
+                                          ct.c_void_p(st.cuda_stream), ct.byref(flops)))
+        e1.record(st)
+        e1.synchronize()
+        if i:
+            times.append(e0.elapsed_time(e1))
+    return flops.value / (float(np.median(times)) / 1e3) / 1e12
+
+
 def epic_plan_create(*args, **kw) -> Plan:
     return Plan(*args, **kw)
 
