@@ -229,6 +229,42 @@ epic_status epical_configure(epic_plan_t plan, double cal_l, double cal_m,
  * Errors: STATE (not configured, or no frames since the last update). */
 epic_status epical_update(epic_plan_t plan, double* d_gains_out, int* d_status);
 
+/* Multiple-pixel and direction-dependent EPICal (Sec. 6, "Multiple pixel
+ * correlations"): correlate every raw antenna signal with the E-field at
+ * n_pix calibration pixels instead of the single calibrator pixel, to bring
+ * more of the sky's power into the loop at O(Na n_pix) per sample.
+ * pix_lm: host [n_pix][2] directions (l, m), each mapped to its nearest
+ * pixel centre (two directions on one pixel give INVALID_ARG).  Uses the
+ * model sources and gamma of the preceding epical_configure.  Per channel
+ * and pixel p the plan forms A_{p,a} (exact response of pixel p to antenna
+ * a) and D_{p,a} = sum_{b != a} conj(A_{p,b}) V^M_ab.  From then on
+ * epic_image stores E'(s_p, t) of every frame and correlates,
+ * K_{a,p} += E_a(t) conj(E'(s_p, t)) (Eq. 12 per pixel, a [Na x T] by
+ * [T x n_pix] product per channel), and epical_update applies, with
+ * C_{a,p} = <K_{a,p}> - conj(A_{p,a}) <P_a> / conj(g_a) (Eq. 15 per pixel):
+ *   imaging gains   g_a <- (1 - gamma) sum_p conj(D_{p,a}) C_{a,p} /
+ *                          sum_p |D_{p,a}|^2 + gamma g_a
+ *                   (least squares over the pixels of the fixed point
+ *                   C_{a,p} = g_a D_{p,a}; Eq. 16 when n_pix = 1),
+ *   per direction   g_{a,p} <- (1 - gamma) C_{a,p} / D_{p,a} + gamma g_{a,p}
+ *                   (each pixel solved independently, Eqs. 16-17),
+ * holding flagged antennas, vanishing denominators and non-finite results
+ * as epical_update does.  Per-direction solutions start from the current
+ * gains.  Resets the accumulators.  epical_configure returns the plan to the
+ * single-pixel form.  The multiple-pixel sums are not part of
+ * epical_get_state.  Needs the fused FP32 path (N <= 128), else
+ * UNSUPPORTED; epic_image_host_static refuses plans in this form (it needs
+ * the tap buffer, plan scratch of T x C x n_pix complex64, grown by
+ * epic_image on demand).  Synchronous.
+ * Errors: STATE (EPICal not configured), INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+epic_status epical_configure_pixels(epic_plan_t plan, int n_pix, const double* pix_lm);
+
+/* Per-direction gain solutions of the multiple-pixel form to host
+ * [C][Na][n_pix] complex128 (pixels in the order given to
+ * epical_configure_pixels).  Synchronous.  Errors: STATE if the plan is not
+ * in the multiple-pixel form. */
+epic_status epical_get_direction_gains(epic_plan_t plan, double* h_gains);
+
 /* Gains taken as constant across a band of channels (Sec. 5: the LWA
  * demonstration averages the per-channel solutions across its central
  * channels to raise the signal to noise).  For every unflagged antenna the

@@ -28,7 +28,8 @@ EXPORTS = [
     "epic_plan_sync", "epical_get_gains", "epical_get_state", "epical_set_state",
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
     "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
-    "epic_graph_launch", "epic_measure_fma_peak",
+    "epic_graph_launch", "epic_measure_fma_peak", "epical_configure_pixels",
+    "epical_get_direction_gains",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -116,6 +117,8 @@ def load(path: str | None = None) -> ct.CDLL:
         "epic_graph_capture": [P, P, ct.c_longlong, P, P],
         "epic_graph_launch": [P],
         "epic_measure_fma_peak": [ct.c_int, ct.c_int, ct.c_longlong, P, P, c_dp],
+        "epical_configure_pixels": [P, ct.c_int, c_dp],
+        "epical_get_direction_gains": [P, c_dp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -243,6 +243,19 @@ class Plan:
             src.ctypes.data_as(B.c_dp), float(gamma),
             None if g is None else g.ctypes.data_as(B.c_dp)))
 
+    def configure_pixels(self, pix_lm):
+        """Multiple-pixel / direction-dependent EPICal (Sec. 6): calibration
+        pixels at the directions pix_lm [P][2] (l, m); after epical_configure."""
+        pl = _f64(pix_lm).reshape(-1, 2)
+        self.n_pix = pl.shape[0]
+        B.check(self._lib.epical_configure_pixels(self.handle, self.n_pix, pl.ctypes.data_as(B.c_dp)))
+
+    def direction_gains(self) -> np.ndarray:
+        """Per-direction solutions [C][Na][P] complex128 (host)."""
+        out = np.empty((self.n_chan, self.n_ant, self.n_pix), np.complex128)
+        B.check(self._lib.epical_get_direction_gains(self.handle, out.view(np.float64).ctypes.data_as(B.c_dp)))
+        return out
+
     def update(self, gains_out=None, status=None):
         torch = _torch()
         B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),

@@ -46,6 +46,12 @@ struct ImageArgs {
   int rs;                  // row stride of the transposed (swizzled) buffer
   int grid;                // CTAs launched
   size_t smem;             // dynamic shared memory bytes
+  // multiple-pixel EPICal (0 pixels = off): the column-pass owner of each
+  // calibration pixel stores E'(s_p, t) to ptap[t][C][npix] (tap order)
+  int npix;
+  const uint2* ptab;       // [COLROUNDS][BT] (slot mask, first tap index) per thread
+  const float2* pph;       // [C][npix] window-coordinate phase of each pixel
+  float2* ptap;            // [T][C][npix] pixel taps of the call
 };
 
 // Shape facts of the fused image kernel for grid side n.
@@ -56,6 +62,45 @@ struct ImageKernelShape {
 };
 
 bool image_kernel_shape(int n, ImageKernelShape* out);
+// Owner of image pixel (kx, ky) in the fused kernel's column pass: column
+// round, thread index and register slot.
+struct PixelOwner {
+  int round, thread, slot;
+};
+bool image_pixel_owner(int n, int kx, int ky, PixelOwner* out);
+int image_col_rounds(int n);
+
+// Multiple-pixel EPICal (epic_multipix.cu).
+struct MultiCorrArgs {
+  const void* volt;        // device [T][C][Na] of the call
+  int input_fmt;
+  long long n_time;
+  int n_chan, n_ant, npix;
+  const float* vscale;     // [C] or nullptr
+  const int* cell0;        // [C][Na]; < 0 = flagged (skipped)
+  const float2* ptap;      // [T][C][npix] pixel taps
+  double2* kmp;            // [C][Na][npix] sum_t E_a conj(tap_p)
+  int segs;                // time segments per channel
+};
+cudaError_t launch_correlate_multi(const MultiCorrArgs& a, cudaStream_t s);
+struct MultiUpdateArgs {
+  int n_chan, n_ant, npix;
+  double2* kmp;            // [C][Na][npix], cleared
+  double2* kacc;           // [C][Na] single-pixel sums, cleared
+  double* pacc;            // [C][Na], cleared
+  double inv_frames;
+  const double2* ap;       // [C][npix][Na] A_{p,a}
+  const double2* dp;       // [C][npix][Na] D_{p,a}
+  double2* gain;           // [C][Na] imaging gains (joint solution)
+  float2* wgain;           // [C][Na] 1/g
+  double2* gdir;           // [C][Na][npix] per-direction solutions
+  const unsigned char* flags;
+  double gamma, dmin;
+  double2* gout;           // [C][Na] or nullptr
+  int* status;             // [C][Na] or nullptr
+  int* held_count;
+};
+cudaError_t launch_update_multi(const MultiUpdateArgs& a, cudaStream_t s);
 int image_rs(int rows_alloc);
 int image_rs_fused(int rows_alloc);
 

@@ -339,6 +339,21 @@ __device__ __forceinline__ void fused_unit(const ImageArgs& A, int c, long long 
             for (int q = 0; q < N2; ++q)
               if (q == pslot) pixs[f] = cmul(v[q], pph);
           }
+          if (A.npix) {
+            // multiple-pixel EPICal: this thread's calibration pixels of
+            // the round (slot mask, index of its first tap)
+            const uint2 tb = __ldg(A.ptab + r * BT + tid);
+            if (tb.x) {
+              float2* dst = A.ptap + (static_cast<size_t>(t + f) * A.n_chan + c) * A.npix;
+              const float2* ph = A.pph + static_cast<size_t>(c) * A.npix;
+#pragma unroll
+              for (int q = 0; q < N2; ++q)
+                if ((tb.x >> q) & 1u) {
+                  const int pi = static_cast<int>(tb.y) + __popc(tb.x & ((1u << q) - 1u));
+                  dst[pi] = cmul(v[q], __ldg(ph + pi));
+                }
+            }
+          }
         }
       }
     }
@@ -871,6 +886,36 @@ cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigne
 cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s) {
   set_gains_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, g_in, g, w);
   return cudaGetLastError();
+}
+
+template <int N>
+void owner_n(int kx, int ky, PixelOwner* o) {
+  using G = Geo<N>;
+  const int m = ky / G::N1;
+  o->round = kx / G::GROUPS;
+  o->thread = (kx % G::GROUPS) * G::N1 + ky % G::N1;
+  o->slot = (m % G::H) * G::N1 + m / G::H;
+}
+
+bool image_pixel_owner(int n, int kx, int ky, PixelOwner* out) {
+  if (kx < 0 || ky < 0 || kx >= n || ky >= n) return false;
+  switch (n) {
+    case 16: owner_n<16>(kx, ky, out); return true;
+    case 32: owner_n<32>(kx, ky, out); return true;
+    case 64: owner_n<64>(kx, ky, out); return true;
+    case 128: owner_n<128>(kx, ky, out); return true;
+    default: return false;
+  }
+}
+
+int image_col_rounds(int n) {
+  switch (n) {
+    case 16: return Geo<16>::COLROUNDS;
+    case 32: return Geo<32>::COLROUNDS;
+    case 64: return Geo<64>::COLROUNDS;
+    case 128: return Geo<128>::COLROUNDS;
+    default: return 0;
+  }
 }
 
 int image_window_stride(int n) {

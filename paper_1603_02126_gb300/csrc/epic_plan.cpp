@@ -159,6 +159,18 @@ struct epic_plan_s {
   int cs = 0, rpc_alloc = 0, clusters = 0, cl_step = 1;
   DevBuf<int> d_rowcol, d_order;
   DevBuf<int2> d_ranges;
+
+  // multiple-pixel / direction-dependent EPICal (Sec. 6); npix = 0: off
+  std::vector<double> model;    // [n_src][3] (l, m, S) given to epical_configure
+  int npix = 0;
+  std::vector<int> pix_user;    // tap index -> caller's pixel index
+  DevBuf<double2> d_ap, d_dp;   // [C][npix][Na] A_{p,a}, D_{p,a} (tap order)
+  DevBuf<double2> d_kmp;        // [C][Na][npix] correlation sums
+  DevBuf<double2> d_gdir;       // [C][Na][npix] per-direction solutions
+  DevBuf<uint2> d_ptab;         // [COLROUNDS][BT] slot mask and first tap per thread
+  DevBuf<float2> d_pph;         // [C][npix] window-coordinate pixel phases
+  DevBuf<float2> d_ptap;        // [ptap_time][C][npix] pixel taps of a call
+  long long ptap_time = 0;
 };
 
 namespace {
@@ -181,6 +193,92 @@ int choose_segments(int n_chan, long long n_time, int ctas, int target = 4) {
     if (units >= 4LL * target * ctas) return static_cast<int>(s);
   }
   return static_cast<int>(best);
+}
+
+// A_{p,a} of channel c: exact response of image pixel (kx, ky) to antenna a
+// through its stencil, (1/Na) sum_taps W_a(j) e^{+2 pi i (j - N/2).(k - N/2)/N}.
+void pixel_response(epic_plan_t p, int c, int kx, int ky, std::vector<std::complex<double>>& A) {
+  const int Na = p->na, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
+  A.assign(Na, 0.0);
+  for (int a = 0; a < Na; ++a) {
+    if (p->flags[a]) continue;
+    const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+    const int bx = p->base[ob], by = p->base[ob + 1];
+    const double* wa = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
+    std::complex<double> s = 0.0;
+    for (int dy = 0; dy < K; ++dy)
+      for (int dx = 0; dx < K; ++dx) {
+        const int jx = bx + dx - h, jy = by + dy - h;
+        long long m = static_cast<long long>(jx - N / 2) * (kx - N / 2) +
+                      static_cast<long long>(jy - N / 2) * (ky - N / 2);
+        m %= N;
+        if (m < 0) m += N;
+        const double ph = 2.0 * kPi * static_cast<double>(m) / N;
+        s += wa[dy * K + dx] * std::complex<double>(std::cos(ph), std::sin(ph));
+      }
+    A[a] = s / static_cast<double>(Na);
+  }
+}
+
+// D_a = sum_{b != a, unflagged} conj(A_b) V^M_ab for channel c with V^M
+// from the point-source model: sum_s S_s e^{-2 pi i u_a.s} (B_s - conj(A_a)
+// e^{+2 pi i u_a.s}), B_s = sum_b conj(A_b) e^{+2 pi i u_b.s}.
+void model_denominator(epic_plan_t p, int c, const std::vector<std::complex<double>>& A,
+                       std::vector<std::complex<double>>& D) {
+  const int Na = p->na;
+  const double f = p->freq[c];
+  D.assign(Na, 0.0);
+  const size_t n_src = p->model.size() / 3;
+  std::vector<std::complex<double>> ph(Na);
+  for (size_t si = 0; si < n_src; ++si) {
+    const double l = p->model[3 * si], m = p->model[3 * si + 1], S = p->model[3 * si + 2];
+    std::complex<double> B = 0.0;
+    for (int b = 0; b < Na; ++b) {
+      const double ux = (p->ant[2 * b] * f) / kC, uy = (p->ant[2 * b + 1] * f) / kC;
+      const double arg = 2.0 * kPi * (ux * l + uy * m);
+      ph[b] = std::complex<double>(std::cos(arg), std::sin(arg));  // e^{+2 pi i u_b.s}
+      if (!p->flags[b]) B += std::conj(A[b]) * ph[b];
+    }
+    for (int a = 0; a < Na; ++a) D[a] += S * (std::conj(ph[a]) * B - std::conj(A[a]));
+  }
+}
+
+// Nearest pixel centre of direction (l, m): l = (k - N/2) / (N du).
+bool nearest_pixel(epic_plan_t p, double l, double m, int* kx, int* ky) {
+  const int N = p->n;
+  const double kxd = std::floor(l * N * p->cell + N / 2 + 0.5);
+  const double kyd = std::floor(m * N * p->cell + N / 2 + 0.5);
+  if (!(kxd >= 0 && kxd < N && kyd >= 0 && kyd < N)) return false;
+  *kx = static_cast<int>(kxd);
+  *ky = static_cast<int>(kyd);
+  return true;
+}
+
+// Window-coordinate phase of pixel (kx, ky) in channel c:
+// (-1)^(kx+ky) e^{2 pi i (x0 kx + y0 ky) / N}.
+float2 window_phase(epic_plan_t p, int c, int kx, int ky) {
+  const int N = p->n;
+  const double sg = ((kx + ky) & 1) ? -1.0 : 1.0;
+  long long m = static_cast<long long>(p->x0[c]) * kx + static_cast<long long>(p->y0[c]) * ky;
+  m %= N;
+  if (m < 0) m += N;
+  const double th = 2.0 * kPi * static_cast<double>(m) / N;
+  return make_float2(static_cast<float>(sg * std::cos(th)), static_cast<float>(sg * std::sin(th)));
+}
+
+// Tap buffer of the multiple-pixel form for calls of up to n_time samples
+// (grown outside any stream capture: epic_graph_capture sizes it first).
+epic_status ensure_ptap(epic_plan_t p, long long n_time) {
+  if (p->npix < 1 || p->ptap_time >= n_time) return EPIC_OK;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream sync before tap buffer growth");
+  e = p->d_ptap.alloc(static_cast<size_t>(n_time) * p->nc * p->npix);
+  if (e != cudaSuccess) {
+    p->ptap_time = 0;
+    return fail(EPIC_ERR_OOM, "pixel tap buffer allocation failed");
+  }
+  p->ptap_time = n_time;
+  return EPIC_OK;
 }
 
 // Arguments of one fused launch over a device batch.
@@ -224,6 +322,7 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   const long long units = static_cast<long long>(p->nc) * a.segs;
   a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
   a.smem = p->smem;
+  a.npix = 0;                              // epic_image arms the pixel taps itself
   return a;
 }
 
@@ -969,6 +1068,13 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_tc_scale.release();
   p->d_tc_pix.release();
   p->d_err.release();
+  p->d_ap.release();
+  p->d_dp.release();
+  p->d_kmp.release();
+  p->d_gdir.release();
+  p->d_ptab.release();
+  p->d_pph.release();
+  p->d_ptap.release();
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   delete p;
@@ -1031,8 +1137,33 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
   if (p->precision != EPIC_PREC_FP32) return image_tc(p, d_volt, n_time, d_image);
   if (p->path == EPIC_PATH_CLUSTER) return image_cluster(p, d_volt, n_time, d_image);
   if (p->path == EPIC_PATH_UNFUSED) return image_unfused(p, d_volt, n_time, d_image);
-  const epic::ImageArgs a = fused_args(p, d_volt, n_time, d_image, 1.0 / static_cast<double>(n_time));
+  epic::ImageArgs a = fused_args(p, d_volt, n_time, d_image, 1.0 / static_cast<double>(n_time));
+  if (p->cal && p->npix > 0) {
+    if (epic_status st = ensure_ptap(p, n_time)) return st;
+    a.npix = p->npix;
+    a.ptab = p->d_ptab.p;
+    a.pph = p->d_pph.p;
+    a.ptap = p->d_ptap.p;
+  }
   EPIC_CUDA(epic::launch_image(p->n, a, p->stream));
+  if (p->cal && p->npix > 0) {
+    epic::MultiCorrArgs m{};
+    m.volt = d_volt;
+    m.input_fmt = p->input;
+    m.n_time = n_time;
+    m.n_chan = p->nc;
+    m.n_ant = p->na;
+    m.npix = p->npix;
+    m.vscale = p->d_vscale.p;
+    m.cell0 = p->d_cell0.p;
+    m.ptap = p->d_ptap.p;
+    m.kmp = p->d_kmp.p;
+    // about two CTAs per SM, segments of at least 64 samples
+    int segs = 1;
+    while (static_cast<long long>(p->nc) * segs < 2LL * p->sms && n_time / (2 * segs) >= 64) segs *= 2;
+    m.segs = segs;
+    EPIC_CUDA(epic::launch_correlate_multi(m, p->stream));
+  }
   if (p->cal) p->frames += n_time;
   return EPIC_OK;
 }
@@ -1069,54 +1200,20 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   if (epic_status s = check_plan(p)) return s;
   if (!(gamma >= 0.0 && gamma < 1.0)) return fail(EPIC_ERR_INVALID_ARG, "gamma must be in [0, 1)");
   if (n_src < 1 || !src) return fail(EPIC_ERR_INVALID_ARG, "at least one model source is required");
-  const int Na = p->na, C = p->nc, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
-  // nearest pixel centre: l = (k - N/2) / (N du)
-  const double kxd = std::floor(cal_l * N * p->cell + N / 2 + 0.5);
-  const double kyd = std::floor(cal_m * N * p->cell + N / 2 + 0.5);
-  if (!(kxd >= 0 && kxd < N && kyd >= 0 && kyd < N))
-    return fail(EPIC_ERR_INVALID_ARG, "calibrator outside the image");
-  const int k0x = static_cast<int>(kxd), k0y = static_cast<int>(kyd);
+  const int Na = p->na, C = p->nc;
+  int k0x = 0, k0y = 0;
+  if (!nearest_pixel(p, cal_l, cal_m, &k0x, &k0y)) return fail(EPIC_ERR_INVALID_ARG, "calibrator outside the image");
+  for (int si = 0; si < n_src; ++si)
+    for (int j = 0; j < 3; ++j)
+      if (!std::isfinite(src[3 * si + j])) return fail(EPIC_ERR_INVALID_ARG, "model sources must be finite");
+  p->model.assign(src, src + 3 * static_cast<size_t>(n_src));
   const size_t n = static_cast<size_t>(C) * Na;
   std::vector<double2> a0(n), dd(n), g(n);
   std::vector<float2> w(n);
+  std::vector<std::complex<double>> A, D;
   for (int c = 0; c < C; ++c) {
-    const double f = p->freq[c];
-    std::vector<std::complex<double>> A(Na, 0.0);
-    // A_{0,a}: exact response of pixel k0 to antenna a through the stencil
-    for (int a = 0; a < Na; ++a) {
-      if (p->flags[a]) continue;
-      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
-      const int bx = p->base[ob], by = p->base[ob + 1];
-      const double* wa = &p->w64[(static_cast<size_t>(c) * Na + a) * KK];
-      std::complex<double> s = 0.0;
-      for (int dy = 0; dy < K; ++dy)
-        for (int dx = 0; dx < K; ++dx) {
-          const int jx = bx + dx - h, jy = by + dy - h;
-          long long m = static_cast<long long>(jx - N / 2) * (k0x - N / 2) +
-                        static_cast<long long>(jy - N / 2) * (k0y - N / 2);
-          m %= N;
-          if (m < 0) m += N;
-          const double ph = 2.0 * kPi * static_cast<double>(m) / N;
-          s += wa[dy * K + dx] * std::complex<double>(std::cos(ph), std::sin(ph));
-        }
-      A[a] = s / static_cast<double>(Na);
-    }
-    // D_a = sum_{b != a, unflagged} conj(A_b) V^M_ab with V^M from point
-    // sources: sum_s S_s e^{-2 pi i u_a.s} (B_s - conj(A_a) e^{+2 pi i u_a.s}),
-    // B_s = sum_b conj(A_b) e^{+2 pi i u_b.s}.
-    std::vector<std::complex<double>> D(Na, 0.0);
-    for (int si = 0; si < n_src; ++si) {
-      const double l = src[3 * si], m = src[3 * si + 1], S = src[3 * si + 2];
-      std::vector<std::complex<double>> ph(Na);
-      std::complex<double> B = 0.0;
-      for (int b = 0; b < Na; ++b) {
-        const double ux = (p->ant[2 * b] * f) / kC, uy = (p->ant[2 * b + 1] * f) / kC;
-        const double arg = 2.0 * kPi * (ux * l + uy * m);
-        ph[b] = std::complex<double>(std::cos(arg), std::sin(arg));  // e^{+2 pi i u_b.s}
-        if (!p->flags[b]) B += std::conj(A[b]) * ph[b];
-      }
-      for (int a = 0; a < Na; ++a) D[a] += S * (std::conj(ph[a]) * B - std::conj(A[a]));
-    }
+    pixel_response(p, c, k0x, k0y, A);
+    model_denominator(p, c, A, D);
     for (int a = 0; a < Na; ++a) {
       const size_t i = static_cast<size_t>(c) * Na + a;
       a0[i] = make_double2(A[a].real(), A[a].imag());
@@ -1143,16 +1240,9 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
   {
-    // pixel k0 of the window-coordinate transform: sign * e^{2 pi i (x0 k0x + y0 k0y) / N}
+    // pixel k0 of the window-coordinate transform
     std::vector<float2> ph(C);
-    const double sg = ((k0x + k0y) & 1) ? -1.0 : 1.0;
-    for (int c = 0; c < C; ++c) {
-      long long m = static_cast<long long>(p->x0[c]) * k0x + static_cast<long long>(p->y0[c]) * k0y;
-      m %= N;
-      if (m < 0) m += N;
-      const double th = 2.0 * kPi * static_cast<double>(m) / N;
-      ph[c] = make_float2(static_cast<float>(sg * std::cos(th)), static_cast<float>(sg * std::sin(th)));
-    }
+    for (int c = 0; c < C; ++c) ph[c] = window_phase(p, c, k0x, k0y);
     EPIC_CUDA(cudaMemcpyAsync(p->d_pixph.p, ph.data(), C * sizeof(float2), cudaMemcpyHostToDevice,
                               p->stream));
   }
@@ -1165,6 +1255,106 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   p->cal = true;
   p->frames = 0;
   p->iteration = 0;
+  p->npix = 0;                             // single-pixel form until epical_configure_pixels
+  return EPIC_OK;
+}
+
+epic_status epical_configure_pixels(epic_plan_t p, int n_pix, const double* pix_lm) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!p->cal) return fail(EPIC_ERR_STATE, "configure EPICal (model, gamma) before its pixels");
+  if (n_pix < 1 || !pix_lm) return fail(EPIC_ERR_INVALID_ARG, "need n_pix >= 1 and pix_lm");
+  if (p->path != EPIC_PATH_FUSED || p->piped || p->precision != EPIC_PREC_FP32)
+    return fail(EPIC_ERR_UNSUPPORTED, "multiple-pixel EPICal needs the fused FP32 path (N <= 128)");
+  const int Na = p->na, C = p->nc, N = p->n;
+  const int rounds = epic::image_col_rounds(N);
+  epic::ImageKernelShape sh{};
+  epic::image_kernel_shape(N, &sh);
+  // owner of every pixel; taps ordered by (round, thread, slot) so that a
+  // thread's taps of one round are consecutive
+  struct Tap { int round, thread, slot, user, kx, ky; };
+  std::vector<Tap> taps(n_pix);
+  for (int i = 0; i < n_pix; ++i) {
+    int kx = 0, ky = 0;
+    if (!nearest_pixel(p, pix_lm[2 * i], pix_lm[2 * i + 1], &kx, &ky))
+      return fail(EPIC_ERR_INVALID_ARG, "calibration pixel outside the image");
+    epic::PixelOwner o{};
+    if (!epic::image_pixel_owner(N, kx, ky, &o)) return fail(EPIC_ERR_UNSUPPORTED, "grid size");
+    taps[i] = {o.round, o.thread, o.slot, i, kx, ky};
+  }
+  std::sort(taps.begin(), taps.end(), [](const Tap& x, const Tap& y) {
+    return x.round != y.round ? x.round < y.round : x.thread != y.thread ? x.thread < y.thread : x.slot < y.slot;
+  });
+  for (int i = 1; i < n_pix; ++i)
+    if (taps[i].kx == taps[i - 1].kx && taps[i].ky == taps[i - 1].ky)
+      return fail(EPIC_ERR_INVALID_ARG, "two directions map to the same pixel");
+  std::vector<uint2> tab(static_cast<size_t>(rounds) * sh.threads, make_uint2(0u, 0u));
+  for (int i = n_pix - 1; i >= 0; --i) {
+    uint2& e = tab[static_cast<size_t>(taps[i].round) * sh.threads + taps[i].thread];
+    e.x |= 1u << taps[i].slot;
+    e.y = static_cast<unsigned>(i);        // first (lowest) tap index of this thread and round
+  }
+  const size_t nap = static_cast<size_t>(C) * n_pix * Na;
+  std::vector<double2> ap(nap), dp(nap);
+  std::vector<float2> pph(static_cast<size_t>(C) * n_pix);
+  std::vector<std::complex<double>> A, D;
+  for (int c = 0; c < C; ++c)
+    for (int i = 0; i < n_pix; ++i) {
+      pixel_response(p, c, taps[i].kx, taps[i].ky, A);
+      model_denominator(p, c, A, D);
+      for (int a = 0; a < Na; ++a) {
+        const size_t o = (static_cast<size_t>(c) * n_pix + i) * Na + a;
+        ap[o] = make_double2(A[a].real(), A[a].imag());
+        dp[o] = make_double2(D[a].real(), D[a].imag());
+      }
+      pph[static_cast<size_t>(c) * n_pix + i] = window_phase(p, c, taps[i].kx, taps[i].ky);
+    }
+  // per-direction solutions start from the current imaging gains
+  const size_t n = static_cast<size_t>(C) * Na;
+  std::vector<double2> g(n), gd(n * n_pix);
+  EPIC_CUDA(cudaMemcpyAsync(g.data(), p->d_gain.p, n * sizeof(double2), cudaMemcpyDeviceToHost, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  for (size_t i = 0; i < n; ++i)
+    for (int q = 0; q < n_pix; ++q) gd[i * n_pix + q] = g[i];
+  cudaError_t es[] = {p->d_ap.alloc(nap), p->d_dp.alloc(nap), p->d_kmp.alloc(n * n_pix),
+                      p->d_gdir.alloc(n * n_pix), p->d_ptab.alloc(tab.size()), p->d_pph.alloc(pph.size())};
+  for (cudaError_t x : es)
+    if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "multiple-pixel EPICal allocation failed");
+  p->d_ptap.release();
+  p->ptap_time = 0;
+  EPIC_CUDA(cudaMemcpyAsync(p->d_ap.p, ap.data(), nap * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_dp.p, dp.data(), nap * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_gdir.p, gd.data(), gd.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                            p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_ptab.p, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                            p->stream));
+  EPIC_CUDA(cudaMemcpyAsync(p->d_pph.p, pph.data(), pph.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                            p->stream));
+  EPIC_CUDA(cudaMemsetAsync(p->d_kmp.p, 0, n * n_pix * sizeof(double2), p->stream));
+  EPIC_CUDA(cudaMemsetAsync(p->d_kacc.p, 0, n * sizeof(double2), p->stream));
+  EPIC_CUDA(cudaMemsetAsync(p->d_pacc.p, 0, n * sizeof(double), p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  p->pix_user.resize(n_pix);
+  for (int i = 0; i < n_pix; ++i) p->pix_user[i] = taps[i].user;
+  p->npix = n_pix;
+  p->frames = 0;
+  return EPIC_OK;
+}
+
+epic_status epical_get_direction_gains(epic_plan_t p, double* h_gains) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!h_gains) return fail(EPIC_ERR_INVALID_ARG, "NULL output");
+  if (p->npix < 1) return fail(EPIC_ERR_STATE, "multiple-pixel EPICal is not configured");
+  const size_t n = static_cast<size_t>(p->nc) * p->na, P = p->npix;
+  std::vector<double2> gd(n * P);
+  EPIC_CUDA(cudaMemcpyAsync(gd.data(), p->d_gdir.p, gd.size() * sizeof(double2), cudaMemcpyDeviceToHost,
+                            p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  for (size_t i = 0; i < n; ++i)
+    for (size_t q = 0; q < P; ++q) {
+      const size_t o = (i * P + static_cast<size_t>(p->pix_user[q])) * 2;
+      h_gains[o] = gd[i * P + q].x;
+      h_gains[o + 1] = gd[i * P + q].y;
+    }
   return EPIC_OK;
 }
 
@@ -1181,6 +1371,31 @@ epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
   if (epic_status s = check_plan(p)) return s;
   if (!p->cal) return fail(EPIC_ERR_STATE, "EPICal is not configured");
   if (p->frames < 1) return fail(EPIC_ERR_STATE, "no frames imaged since the last update");
+  if (p->npix > 0) {
+    epic::MultiUpdateArgs m{};
+    m.n_chan = p->nc;
+    m.n_ant = p->na;
+    m.npix = p->npix;
+    m.kmp = p->d_kmp.p;
+    m.kacc = p->d_kacc.p;
+    m.pacc = p->d_pacc.p;
+    m.inv_frames = 1.0 / static_cast<double>(p->frames);
+    m.ap = p->d_ap.p;
+    m.dp = p->d_dp.p;
+    m.gain = p->d_gain.p;
+    m.wgain = p->d_wgain.p;
+    m.gdir = p->d_gdir.p;
+    m.flags = p->d_flags.p;
+    m.gamma = p->gamma;
+    m.dmin = kDmin;
+    m.gout = reinterpret_cast<double2*>(d_gains_out);
+    m.status = d_status;
+    m.held_count = p->d_held.p;
+    EPIC_CUDA(epic::launch_update_multi(m, p->stream));
+    p->frames = 0;
+    p->iteration += 1;
+    return EPIC_OK;
+  }
   epic::UpdateArgs u{};
   u.n_chan = p->nc;
   u.n_ant = p->na;
@@ -1408,6 +1623,7 @@ epic_status epic_graph_capture(epic_plan_t p, const void* d_volt, long long n_ti
   if (!p->stream) return fail(EPIC_ERR_INVALID_ARG, "graph capture needs a non-default plan stream");
   if (p->cal && p->frames != 0)
     return fail(EPIC_ERR_STATE, "update EPICal before capturing (frames are pending)");
+  if (epic_status st = ensure_ptap(p, n_time)) return st;    // multiple-pixel taps
   if (p->path == EPIC_PATH_UNFUSED) {
     // allocate the batch scratch outside the capture
     const bool cal = p->cal;
@@ -1534,6 +1750,8 @@ int image_batch_scaled(epic_plan_s* p, const void* d_volt, long long n_time, dou
   if (!p || !d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad batch");
   if (p->path != EPIC_PATH_FUSED)
     return fail(EPIC_ERR_UNSUPPORTED, "this call needs a plan on the fused path");
+  if (p->cal && p->npix > 0)
+    return fail(EPIC_ERR_UNSUPPORTED, "multiple-pixel EPICal needs its tap buffer (plan scratch)");
   const ImageArgs a = fused_args(p, d_volt, n_time, d_image, img_scale);
   cudaError_t e = launch_image(p->n, a, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "image launch");
