@@ -353,7 +353,70 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
     }
     p4.close()
     pe.close()
+    out["noise_trends"] = noise_trends(torch, Plan, dev, stream, run)
     return out
+
+
+def noise_trends(torch, Plan, dev, stream, run):
+    """Sec. 4 noise-trend sweep on the LWA-like array (64 channels, 4-bit):
+    EPICal (10 loops of t_cal from the true gains, gamma = 0.35) against the
+    visibility solve of Eq. 21 on visibilities of the last t_eff = t_cal (1 +
+    gamma) / (1 - gamma) samples of the same stream, each with the full sky
+    model and with the calibrator alone; sigma_g of Eq. 22 after removing
+    each channel's global phase, and the GPU time of each stage."""
+    w = synth.workload("noise")
+    C, Na = len(w["freqs"]), w["ant_xy"].shape[0]
+    gam = w["gamma"]
+    sc = stream.cuda_stream
+
+    def sig(g):
+        ph = np.angle(np.sum(g, axis=1, keepdims=True))     # true gains are 1
+        return float(np.sqrt(np.mean(np.abs(g * np.exp(-1j * ph) - 1.0) ** 2)))
+
+    res = {"workload": "Sec. 4 sky (5 Jy calibrator + 49 sources of 0.2-0.5 Jy) on the LWA-like array, "
+                       "C=64, N=128, 4-bit, true gains 1", "rows": []}
+    for noise in (10.0, 100.0):
+        rms = np.sqrt((w["sky"][:, 2].sum() + noise) / 2)
+        lsb = np.full(C, rms / 2.0)
+        for t_cal in (128, 512, 2048):
+            t_eff = int(round(t_cal * (1 + gam) / (1 - gam)))
+            T = 10 * t_cal
+            v = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], T, noise, lsb,
+                                         seed=int(noise) * 7919 + t_cal, device=dev)
+            row = {"sigma_r": noise, "t_cal": t_cal, "t_eff": t_eff}
+            for name, model in (("full", w["model"]), ("single", w["model_single"])):
+                p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, input="ci4", voltage_scale=lsb, stream=sc)
+                p.configure((0.0, 0.0), model, gam)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for k in range(10):
+                    p.image(v[k * t_cal:(k + 1) * t_cal])
+                    p.update()
+                e1.record(stream)
+                e1.synchronize()
+                row[f"epical_{name}_sigma_g"] = sig(p.gains())
+                row[f"epical_{name}_ms"] = e0.elapsed_time(e1)
+                vwin = v[T - t_eff:]
+                vis = p.visibilities(vwin)
+                ms_x = run(lambda: p.visibilities(vwin, vis), 3)
+                gv = torch.ones((C, Na), dtype=torch.complex128, device=dev)
+                e0.record(stream)
+                it = p.visibility_solve(vis, gv, max_iter=2000, tol=1e-10)
+                e1.record(stream)
+                e1.synchronize()
+                row[f"vis_{name}_sigma_g"] = sig(gv.cpu().numpy())
+                row[f"xengine_ms"] = ms_x
+                row[f"solve_{name}_ms"] = e0.elapsed_time(e1)
+                row[f"solve_{name}_iters_max"] = int(it.max())
+                p.close()
+            row["epical_over_vis_full"] = row["epical_full_sigma_g"] / row["vis_full_sigma_g"]
+            row["epical_over_vis_single"] = row["epical_single_sigma_g"] / row["vis_single_sigma_g"]
+            res["rows"].append(row)
+            del v
+    # algorithmic X-engine work: the Na (Na + 1) / 2 distinct complex products per sample
+    last = res["rows"][-1]
+    res["xengine_tflops"] = 8.0 * Na * (Na + 1) / 2 * C * last["t_eff"] / (last["xengine_ms"] / 1e3) / 1e12
+    return res
 
 
 def profile_case(name):

@@ -236,6 +236,18 @@ def workload(name: str, seed: int | None = None, n_time: int | None = None,
                     kernel_sigma=0.5, gains=gains, sky=sky, model=pts,
                     n_time=n_time or (10000 if name == "lwa" else 4096),
                     noise_power=noise, input="ci4", gamma=0.5, lsb=lsb, rng=rng)
+    if name == "noise":            # Sec. 4 sky on the LWA-like array: 5 Jy + 49 x U[0.2, 0.5] Jy
+        rng = np.random.default_rng(5 if seed is None else seed)
+        na = n_ant or 256
+        ant = layout_ellipse(na, 50.0, 45.0, rng, min_sep_m=2.0)
+        nc = n_chan or 64
+        freqs = channels(nc, 40e6, 80e6)
+        faint = np.column_stack([random_directions(49, rng, 0.5), rng.uniform(0.2, 0.5, 49)])
+        sky = np.vstack([[0.0, 0.0, 5.0], faint])
+        return dict(ant_xy=ant, freqs=freqs, grid_n=128, cell=0.5, kernel_support=3,
+                    kernel_sigma=0.5, gains=np.ones((nc, na), complex), sky=sky, model=sky,
+                    model_single=sky[:1], n_time=n_time or 1024, noise_power=10.0,
+                    input="ci4", gamma=0.35, lsb=None, rng=rng)
     if name == "compact1024":      # Na=1024 in a 200 m disc, 32 ch 40-80 MHz, 256^2, 4-bit
         rng = np.random.default_rng(2 if seed is None else seed)
         na = n_ant or 1024

@@ -265,6 +265,40 @@ epic_status epical_configure_pixels(epic_plan_t plan, int n_pix, const double* p
  * in the multiple-pixel form. */
 epic_status epical_get_direction_gains(epic_plan_t plan, double* h_gains);
 
+/* Visibility-based comparison path (Sec. 4, noise trends; Sec. 5 checks the
+ * LWA solutions the same way).  X-engine: every antenna pair's visibility
+ * from the voltage stream EPICal uses,
+ *   V[c][a][b] (+)= (1/n_time) sum_t E_a(t) conj(E_b(t)),
+ * E_a = voltage_scale[c] x the raw sample (uncalibrated, flags ignored),
+ * autocorrelations included.  d_volt: device [n_time][C][Na] as for
+ * epic_image.  d_vis: device [C][Na][Na] complex128, caller-owned
+ * (Hermitian: both triangles written); accumulate = 0 overwrites, else adds.
+ * For 4-bit input the per-channel sums are exact integers (FP32 holds them
+ * exactly below 2^24; segments of 32768 samples are added in FP64).
+ * Asynchronous.  Errors: INVALID_ARG, CUDA. */
+epic_status epic_visibilities(epic_plan_t plan, const void* d_volt, long long n_time, double* d_vis,
+                              int accumulate);
+
+/* Visibility-based gain solve: minimise Eq. 21,
+ *   chi^2 = sum_a sum_{b != a} |V_ab - g_a conj(g_b) V^M_ab|^2,
+ * per channel by alternating least squares with every other iterate
+ * averaged (StEFCal, Salvini & Wijnholds 2014; the paper names no solver):
+ *   g_a <- sum_b V_ab g_b conj(V^M_ab) / sum_b |g_b V^M_ab|^2
+ * over unflagged b != a with |u_a - u_b| >= min_baseline wavelengths (Sec. 5
+ * leaves out baselines shorter than 10 wavelengths; 0 keeps all), until
+ * max_a |g_new - g| <= tol max_a |g_new| or max_iter iterations.  V^M is
+ * formed from the point-source model of the last epical_configure
+ * (V^M_ab = sum_s S_s e^{-2 pi i (u_a - u_b) . s}; the plan then holds
+ * C x Na x Na complex128 of it).  d_vis: device [C][Na][Na] complex128 (as
+ * from epic_visibilities).  d_gains: device [C][Na] complex128, the start
+ * on input and the solution on output; flagged antennas and antennas with
+ * no usable pair keep their start value.  h_iters: host [C] iterations
+ * used, or NULL (then the call is asynchronous; else synchronous).  FP64.
+ * Errors: STATE (EPICal not configured), INVALID_ARG, UNSUPPORTED
+ * (Na > 6400), OOM, CUDA. */
+epic_status epic_visibility_solve(epic_plan_t plan, const double* d_vis, double* d_gains, int max_iter,
+                                  double tol, double min_baseline, int* h_iters);
+
 /* Gains taken as constant across a band of channels (Sec. 5: the LWA
  * demonstration averages the per-channel solutions across its central
  * channels to raise the signal to noise).  For every unflagged antenna the

@@ -36,7 +36,7 @@ __all__ = [
     "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
     "model_image", "chi2_loss", "chi2_gradient", "average_channels",
     "MultiPixelPlan", "pixel_taps", "correlate_multi", "multipixel_update",
-    "direction_update", "multipixel_interval",
+    "direction_update", "multipixel_interval", "baseline_mask",
 ]
 
 
@@ -545,31 +545,49 @@ def visibilities(E: np.ndarray) -> np.ndarray:
     return (E.T @ np.conj(E)) / E.shape[0]
 
 
-def visibility_solve(V, VM, g0, tol: float = 1e-12, max_iter: int = 5000, flags=None):
+def baseline_mask(uv: np.ndarray, min_baseline: float) -> np.ndarray:
+    """Pairs (a, b) used by the visibility solve: a != b and |u_a - u_b| >=
+    min_baseline wavelengths (Sec. 5 leaves out baselines shorter than 10
+    wavelengths, where the diffuse sky is not modelled).  uv: [Na][2]."""
+    d = np.hypot(uv[:, None, 0] - uv[None, :, 0], uv[:, None, 1] - uv[None, :, 1])
+    m = d >= min_baseline
+    np.fill_diagonal(m, False)
+    return m
+
+
+def visibility_solve(V, VM, g0, tol: float = 1e-12, max_iter: int = 5000, flags=None,
+                     pair_mask=None, return_iters: bool = False):
     """Minimise chi^2 = sum_a sum_{b != a} |V_ab - g_a conj(g_b) V^M_ab|^2
     (Eq. 21).  Reading: the paper does not name its solver; this uses the
     alternating least-squares step with every other iterate averaged
     (StEFCal, Salvini & Wijnholds 2014):
-      g_a <- sum_{b!=a} V_ab g_b conj(V^M_ab) / sum_{b!=a} |g_b V^M_ab|^2."""
+      g_a <- sum_{b!=a} V_ab g_b conj(V^M_ab) / sum_{b!=a} |g_b V^M_ab|^2,
+    every antenna from the previous iterate, stopping when
+    max_a |g_new - g| <= tol max_a |g_new|.  pair_mask [Na][Na] (optional)
+    restricts the sums to the listed pairs (baseline_mask); flagged antennas
+    and antennas left without a usable pair keep g0."""
     Na = V.shape[0]
     flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
     use = ~flags
+    pm = ~np.eye(Na, dtype=bool) if pair_mask is None else np.asarray(pair_mask, bool)
     g = np.array(g0, np.complex128)
     for it in range(max_iter):
         gn = g.copy()
         for a in range(Na):
             if flags[a]:
                 continue
-            m = use.copy()
+            m = use & pm[a]
             m[a] = False
             z = g[m] * np.conj(VM[a, m])
-            gn[a] = np.sum(V[a, m] * z) / np.sum(np.abs(z) ** 2)
+            den = np.sum(np.abs(z) ** 2)
+            if den > 0:                    # an antenna with no usable pair keeps its gain
+                gn[a] = np.sum(V[a, m] * z) / den
         if it % 2 == 1:
             gn = 0.5 * (gn + g)
         if np.max(np.abs(gn - g)) <= tol * np.max(np.abs(gn)):
-            return gn
+            return (gn, it + 1) if return_iters else gn
         g = gn
-    return g
+    return (g, max_iter) if return_iters else g
 
 
 def align_phase(g_est: np.ndarray, g_true: np.ndarray) -> np.ndarray:

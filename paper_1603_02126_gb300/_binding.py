@@ -29,7 +29,7 @@ EXPORTS = [
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
     "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
     "epic_graph_launch", "epic_measure_fma_peak", "epical_configure_pixels",
-    "epical_get_direction_gains",
+    "epical_get_direction_gains", "epic_visibilities", "epic_visibility_solve",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -119,6 +119,8 @@ def load(path: str | None = None) -> ct.CDLL:
         "epic_measure_fma_peak": [ct.c_int, ct.c_int, ct.c_longlong, P, P, c_dp],
         "epical_configure_pixels": [P, ct.c_int, c_dp],
         "epical_get_direction_gains": [P, c_dp],
+        "epic_visibilities": [P, P, ct.c_longlong, P, ct.c_int],
+        "epic_visibility_solve": [P, P, P, ct.c_int, ct.c_double, ct.c_double, c_ip],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -256,6 +256,28 @@ class Plan:
         B.check(self._lib.epical_get_direction_gains(self.handle, out.view(np.float64).ctypes.data_as(B.c_dp)))
         return out
 
+    def visibilities(self, volt, vis=None, accumulate=False):
+        """X-engine (Sec. 4 comparison): V [C][Na][Na] complex128 on the
+        device from a device voltage batch [T][C][Na]."""
+        torch = _torch()
+        want = torch.uint8 if self.input == "ci4" else torch.complex64
+        if vis is None:
+            vis = torch.empty((self.n_chan, self.n_ant, self.n_ant), dtype=torch.complex128,
+                              device=volt.device)
+        B.check(self._lib.epic_visibilities(self.handle, _dptr(volt, want, "volt"), int(volt.shape[0]),
+                                            _dptr(vis, torch.complex128, "vis"), int(bool(accumulate))))
+        return vis
+
+    def visibility_solve(self, vis, gains, max_iter=5000, tol=1e-12, min_baseline=0.0):
+        """Eq. 21 by StEFCal on the device, in place on gains [C][Na]
+        complex128 (start -> solution).  Returns the iterations per channel."""
+        torch = _torch()
+        it = np.zeros(self.n_chan, np.int32)
+        B.check(self._lib.epic_visibility_solve(self.handle, _dptr(vis, torch.complex128, "vis"),
+                                                _dptr(gains, torch.complex128, "gains"), int(max_iter),
+                                                float(tol), float(min_baseline), it.ctypes.data_as(B.c_ip)))
+        return it
+
     def update(self, gains_out=None, status=None):
         torch = _torch()
         B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),

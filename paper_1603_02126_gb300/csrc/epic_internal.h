@@ -101,6 +101,33 @@ struct MultiUpdateArgs {
   int* held_count;
 };
 cudaError_t launch_update_multi(const MultiUpdateArgs& a, cudaStream_t s);
+
+// Visibility-based comparison path (epic_xengine.cu).
+struct XengineArgs {
+  const void* volt;        // device [T][C][Na]
+  int input_fmt;
+  long long n_time;
+  int n_chan, n_ant;
+  const float* vscale;     // [C] or nullptr
+  double scale;            // 1 / T
+  double2* vis;            // [C][Na][Na], accumulated (atomics)
+};
+cudaError_t launch_xengine(const XengineArgs& a, cudaStream_t s);
+cudaError_t launch_model_vis(int n_chan, int n_ant, int n_src, const double2* ph, const double* flux,
+                             double2* vm, cudaStream_t s);
+struct StefcalArgs {
+  int n_chan, n_ant;
+  const double2* vis;      // [C][Na][Na]
+  const double2* vm;       // [C][Na][Na] model visibilities
+  const double2* uv;       // [C][Na] antenna positions in wavelengths
+  const unsigned char* flags;
+  double min_baseline;     // wavelengths; shorter pairs are left out
+  double tol;
+  int max_iter;
+  double2* gains;          // [C][Na] in: start, out: solution
+  int* iters;              // [C] iterations used, or nullptr
+};
+cudaError_t launch_stefcal(const StefcalArgs& a, cudaStream_t s);
 int image_rs(int rows_alloc);
 int image_rs_fused(int rows_alloc);
 

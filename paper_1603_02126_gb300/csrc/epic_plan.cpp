@@ -171,6 +171,13 @@ struct epic_plan_s {
   DevBuf<float2> d_pph;         // [C][npix] window-coordinate pixel phases
   DevBuf<float2> d_ptap;        // [ptap_time][C][npix] pixel taps of a call
   long long ptap_time = 0;
+
+  // visibility-based comparison (Sec. 4): model visibilities of the
+  // configured model, formed on the first solve after epical_configure
+  DevBuf<double2> d_vm;         // [C][Na][Na]
+  DevBuf<double2> d_uv;         // [C][Na] positions in wavelengths
+  DevBuf<int> d_iters;          // [C] solver iterations
+  bool vm_stale = true;
 };
 
 namespace {
@@ -1075,6 +1082,9 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_ptab.release();
   p->d_pph.release();
   p->d_ptap.release();
+  p->d_vm.release();
+  p->d_uv.release();
+  p->d_iters.release();
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   delete p;
@@ -1256,6 +1266,90 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
   p->frames = 0;
   p->iteration = 0;
   p->npix = 0;                             // single-pixel form until epical_configure_pixels
+  p->vm_stale = true;
+  return EPIC_OK;
+}
+
+epic_status epic_visibilities(epic_plan_t p, const void* d_volt, long long n_time, double* d_vis,
+                              int accumulate) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!d_volt || !d_vis) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
+  if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
+  const size_t nv = static_cast<size_t>(p->nc) * p->na * p->na;
+  if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_vis, 0, nv * sizeof(double2), p->stream));
+  epic::XengineArgs a{};
+  a.volt = d_volt;
+  a.input_fmt = p->input;
+  a.n_time = n_time;
+  a.n_chan = p->nc;
+  a.n_ant = p->na;
+  a.vscale = p->d_vscale.p;
+  a.scale = 1.0 / static_cast<double>(n_time);
+  a.vis = reinterpret_cast<double2*>(d_vis);
+  EPIC_CUDA(epic::launch_xengine(a, p->stream));
+  return EPIC_OK;
+}
+
+epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_gains, int max_iter,
+                                  double tol, double min_baseline, int* h_iters) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!p->cal || p->model.empty()) return fail(EPIC_ERR_STATE, "configure EPICal (the model) first");
+  if (!d_vis || !d_gains || max_iter < 1 || !(tol >= 0.0) || !(min_baseline >= 0.0))
+    return fail(EPIC_ERR_INVALID_ARG, "bad solve arguments");
+  const int C = p->nc, Na = p->na;
+  const size_t nv = static_cast<size_t>(C) * Na * Na;
+  if (static_cast<size_t>(2) * Na * sizeof(double2) > 200 * 1024)
+    return fail(EPIC_ERR_UNSUPPORTED, "visibility solve holds 2 x Na complex128 gains in shared memory (Na <= 6400)");
+  if (p->vm_stale || !p->d_vm.p) {
+    // phasors e_a(s) = e^{-2 pi i u_a . s} in FP64 on the host, V^M on the device
+    const int ns = static_cast<int>(p->model.size() / 3);
+    std::vector<double2> ph(static_cast<size_t>(C) * ns * Na);
+    std::vector<double> flux(ns);
+    std::vector<double2> uv(static_cast<size_t>(C) * Na);
+    for (int si = 0; si < ns; ++si) flux[si] = p->model[3 * si + 2];
+    for (int c = 0; c < C; ++c) {
+      const double f = p->freq[c];
+      for (int a = 0; a < Na; ++a)
+        uv[static_cast<size_t>(c) * Na + a] = make_double2((p->ant[2 * a] * f) / kC, (p->ant[2 * a + 1] * f) / kC);
+      for (int si = 0; si < ns; ++si)
+        for (int a = 0; a < Na; ++a) {
+          const double2 u = uv[static_cast<size_t>(c) * Na + a];
+          const double arg = -2.0 * kPi * (u.x * p->model[3 * si] + u.y * p->model[3 * si + 1]);
+          ph[(static_cast<size_t>(c) * ns + si) * Na + a] = make_double2(std::cos(arg), std::sin(arg));
+        }
+    }
+    DevBuf<double2> d_ph;
+    DevBuf<double> d_flux;
+    cudaError_t es[] = {p->d_vm.alloc(nv), p->d_uv.alloc(uv.size()), p->d_iters.alloc(C), d_ph.alloc(ph.size()),
+                        d_flux.alloc(flux.size())};
+    for (cudaError_t x : es)
+      if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "model visibility allocation failed");
+    EPIC_CUDA(cudaMemcpyAsync(d_ph.p, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
+    EPIC_CUDA(cudaMemcpyAsync(d_flux.p, flux.data(), flux.size() * sizeof(double), cudaMemcpyHostToDevice,
+                              p->stream));
+    EPIC_CUDA(cudaMemcpyAsync(p->d_uv.p, uv.data(), uv.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                              p->stream));
+    EPIC_CUDA(epic::launch_model_vis(C, Na, ns, d_ph.p, d_flux.p, p->d_vm.p, p->stream));
+    EPIC_CUDA(cudaStreamSynchronize(p->stream));   // d_ph, d_flux are freed on return
+    p->vm_stale = false;
+  }
+  epic::StefcalArgs a{};
+  a.n_chan = C;
+  a.n_ant = Na;
+  a.vis = reinterpret_cast<const double2*>(d_vis);
+  a.vm = p->d_vm.p;
+  a.uv = p->d_uv.p;
+  a.flags = p->d_flags.p;
+  a.min_baseline = min_baseline;
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.gains = reinterpret_cast<double2*>(d_gains);
+  a.iters = p->d_iters.p;
+  EPIC_CUDA(epic::launch_stefcal(a, p->stream));
+  if (h_iters) {
+    EPIC_CUDA(cudaMemcpyAsync(h_iters, p->d_iters.p, C * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  }
   return EPIC_OK;
 }
 
