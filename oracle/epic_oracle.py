@@ -36,7 +36,8 @@ __all__ = [
     "align_phase", "Plan", "image_pixels", "correlate_sampled", "pixel_matrix",
     "model_image", "chi2_loss", "chi2_gradient", "average_channels",
     "MultiPixelPlan", "pixel_taps", "correlate_multi", "multipixel_update",
-    "direction_update", "multipixel_interval", "baseline_mask",
+    "direction_update", "multipixel_interval", "baseline_mask", "bandpass_x", "fit_bandpass",
+    "phase_factors",
 ]
 
 
@@ -304,6 +305,57 @@ def average_channels(g, c_lo: int, c_hi: int, flags=None):
     return g
 
 
+def bandpass_x(freqs, c_lo: int, c_hi: int) -> np.ndarray:
+    """Fit abscissa of channels c_lo..c_hi-1: frequency mapped linearly onto
+    [-1, 1] over the band (0 for a one-channel band)."""
+    f = np.asarray(freqs, np.float64)[c_lo:c_hi]
+    lo, hi = f.min(), f.max()
+    if hi == lo:
+        return np.zeros_like(f)
+    return (f - 0.5 * (lo + hi)) / (0.5 * (hi - lo))
+
+
+def fit_bandpass(g, freqs, c_lo: int, c_hi: int, deg_amp: int, deg_phase: int, flags=None):
+    """Gain model fitted across frequency (Sec. 6, "Fitting gain models": a
+    low-order polynomial in amplitude and in phase over a band of channels).
+    Per unflagged antenna: the amplitudes |g| and the phases arg g, unwrapped
+    along the band from its first channel (each step taken within pi), are
+    fitted by least squares with polynomials of degrees deg_amp and deg_phase
+    in the band abscissa x (bandpass_x); the gains of the band are replaced
+    by A(x) e^{i Phi(x)}.  Channels outside the band, flagged antennas and
+    antennas with a zero or non-finite gain in the band are returned
+    unchanged.  g: [C][Na] complex.  Needs c_hi - c_lo > max(deg_amp, deg_phase)."""
+    g = np.array(g, np.complex128, copy=True)
+    C, Na = g.shape
+    if not (0 <= c_lo < c_hi <= C):
+        raise ValueError("need 0 <= c_lo < c_hi <= C")
+    if min(deg_amp, deg_phase) < 0 or c_hi - c_lo <= max(deg_amp, deg_phase):
+        raise ValueError("need 0 <= degree < channels in the band")
+    flags = np.zeros(Na, bool) if flags is None else np.asarray(flags, bool)
+    x = bandpass_x(freqs, c_lo, c_hi)
+    for a in range(Na):
+        ga = g[c_lo:c_hi, a]
+        if flags[a] or not np.all(np.isfinite(ga)) or np.any(ga == 0):
+            continue
+        amp = np.abs(ga)
+        ph = np.unwrap(np.angle(ga))
+        pa = np.polynomial.polynomial.polyfit(x, amp, deg_amp)
+        pp = np.polynomial.polynomial.polyfit(x, ph, deg_phase)
+        g[c_lo:c_hi, a] = (np.polynomial.polynomial.polyval(x, pa)
+                           * np.exp(1j * np.polynomial.polynomial.polyval(x, pp)))
+    return g
+
+
+def phase_factors(ant_xy_m, freq_hz: float, phase_lm) -> np.ndarray:
+    """Phasing to a phase centre s0 = (l0, m0) away from zenith (Sec. 2.1
+    footnote: a phase applied to the electric fields as one phases
+    visibilities): p_a = exp(+2 pi i u_a . s0) for the planar array, so that
+    p_a E_a of a source at s equals the unphased field of a source at s - s0
+    and the image is centred on s0 (pixel l = l0 + (kx - N/2)/(N du))."""
+    uv = antenna_uv(ant_xy_m, freq_hz)
+    return np.exp(2j * np.pi * (uv[:, 0] * phase_lm[0] + uv[:, 1] * phase_lm[1]))
+
+
 # --------------------------------------------------------------------------
 # one calibration interval for all channels
 # --------------------------------------------------------------------------
@@ -313,7 +365,7 @@ class Plan:
 
     def __init__(self, ant_xy_m, freq_hz, grid_n, cell, kernel="gaussian",
                  support=3, param=0.5, flags=None, cal_lm=(0.0, 0.0),
-                 model_lmS=None, n_ant_norm=None):
+                 model_lmS=None, n_ant_norm=None, phase_lm=None):
         self.ant = np.asarray(ant_xy_m, np.float64)
         self.freqs = np.atleast_1d(np.asarray(freq_hz, np.float64))
         self.N = int(grid_n)
@@ -323,9 +375,14 @@ class Plan:
         self.flags = np.zeros(self.Na, bool) if flags is None else np.asarray(flags, bool)
         self.base, self.W = grid_table(self.ant, self.freqs, self.N, self.cell,
                                        kernel, support, param, self.flags)
-        self.k0 = calibrator_pixel(cal_lm[0], cal_lm[1], self.N, self.cell)
+        # phase centre (Sec. 2.1 footnote): E_a phased by p_a, image
+        # coordinates relative to it
+        self.phase_lm = (0.0, 0.0) if phase_lm is None else (float(phase_lm[0]), float(phase_lm[1]))
+        self.phase = np.stack([phase_factors(self.ant, f, self.phase_lm) for f in self.freqs])
+        self.k0 = calibrator_pixel(cal_lm[0] - self.phase_lm[0], cal_lm[1] - self.phase_lm[1],
+                                   self.N, self.cell)
         self.A0 = np.stack([pixel_row(self.base[c], self.W[c], self.N, self.k0, self.norm)
-                            for c in range(len(self.freqs))])
+                            for c in range(len(self.freqs))]) * self.phase
         if model_lmS is not None:
             self.D = np.stack([cal_denominator(self.A0[c],
                                                model_visibilities(self.ant, f, model_lmS),
@@ -346,7 +403,7 @@ def image_interval(plan: Plan, E: np.ndarray, g: np.ndarray, block: int = 256):
     pix = np.zeros((T, C), np.complex128)
     for c in range(C):
         for t0 in range(0, T, block):
-            Ec = apply_gains(E[t0:t0 + block, c, :], g[c])
+            Ec = apply_gains(E[t0:t0 + block, c, :], g[c]) * plan.phase[c]
             G = grid_frames(Ec, plan.base[c], plan.W[c], N, plan.flags)
             Ei = efield_image(G, plan.norm)
             img[c] += (np.abs(Ei) ** 2).sum(axis=0)
@@ -367,7 +424,7 @@ def epical_interval(plan: Plan, E: np.ndarray, g: np.ndarray, gamma: float,
         img = None
         pix = np.zeros((T, C), np.complex128)
         for c in range(C):
-            G = grid_frames(apply_gains(E[:, c, :], g[c]), plan.base[c], plan.W[c],
+            G = grid_frames(apply_gains(E[:, c, :], g[c]) * plan.phase[c], plan.base[c], plan.W[c],
                             plan.N, plan.flags)
             # the single pixel k0 of the Eq. 10 DFT
             n = plan.N
@@ -396,7 +453,7 @@ def image_pixels(plan: Plan, E: np.ndarray, g: np.ndarray, c: int, pixels,
     j = np.arange(n) - n // 2
     out = np.zeros(len(pixels))
     for t0 in range(0, T, block):
-        G = grid_frames(apply_gains(E[t0:t0 + block, c, :], g[c]), plan.base[c],
+        G = grid_frames(apply_gains(E[t0:t0 + block, c, :], g[c]) * plan.phase[c], plan.base[c],
                         plan.W[c], n, plan.flags)
         for i, (kx, ky) in enumerate(pixels):
             fx = np.exp(2j * np.pi * np.mod(j * (kx - n // 2), n) / n)
@@ -417,7 +474,7 @@ def correlate_sampled(plan: Plan, E: np.ndarray, g: np.ndarray, c: int, ants,
     fy = np.exp(2j * np.pi * np.mod(j * (plan.k0[1] - n // 2), n) / n)
     pix = np.zeros(T, np.complex128)
     for t0 in range(0, T, block):
-        G = grid_frames(apply_gains(E[t0:t0 + block, c, :], g[c]), plan.base[c],
+        G = grid_frames(apply_gains(E[t0:t0 + block, c, :], g[c]) * plan.phase[c], plan.base[c],
                         plan.W[c], n, plan.flags)
         pix[t0:t0 + block] = np.einsum("tyx,y,x->t", G, fy, fx) / plan.norm
     Kc, P = correlate(E[:, c, list(ants)], pix)
@@ -438,11 +495,11 @@ class MultiPixelPlan(Plan):
 
     def __init__(self, ant_xy_m, freq_hz, grid_n, cell, pix_lm, model_lmS, **kw):
         super().__init__(ant_xy_m, freq_hz, grid_n, cell, model_lmS=model_lmS, **kw)
-        self.pix = [calibrator_pixel(l, m, self.N, self.cell)
+        self.pix = [calibrator_pixel(l - self.phase_lm[0], m - self.phase_lm[1], self.N, self.cell)
                     for l, m in np.asarray(pix_lm, np.float64).reshape(-1, 2)]
         C = len(self.freqs)
         self.Ap = np.stack([np.stack([pixel_row(self.base[c], self.W[c], self.N, k, self.norm)
-                                      for k in self.pix]) for c in range(C)])      # [C][P][Na]
+                                      * self.phase[c] for k in self.pix]) for c in range(C)])  # [C][P][Na]
         self.Dp = np.stack([np.stack([cal_denominator(self.Ap[c, i],
                                                       model_visibilities(self.ant, f, model_lmS),
                                                       self.flags)
@@ -529,7 +586,7 @@ def multipixel_interval(plan: MultiPixelPlan, E: np.ndarray, g: np.ndarray, gdir
     Ps = np.empty(g.shape)
     held = np.zeros(g.shape, bool)
     for c in range(C):
-        taps = pixel_taps(plan, apply_gains(E[:, c, :], g[c]), c, plan.pix)
+        taps = pixel_taps(plan, apply_gains(E[:, c, :], g[c]) * plan.phase[c], c, plan.pix)
         Ks[c], Ps[c] = correlate_multi(E[:, c, :], taps)
         gn[c], held[c], Cc = multipixel_update(Ks[c], Ps[c], plan.Ap[c], plan.Dp[c], g[c],
                                                gamma, plan.flags, d_min)
@@ -611,7 +668,8 @@ def gain_error(g_est: np.ndarray, g_true: np.ndarray) -> float:
 def pixel_matrix(plan: Plan, c: int) -> np.ndarray:
     """A_{k,a} for every pixel k of channel c ([N*N][Na], k = ky*N + kx):
     the response of pixel k to antenna a through gridding (Eq. 9) and the
-    Eq. 10 transform, E'(s_k) = sum_a A_{k,a} E'_a.  Explicit sums over taps."""
+    Eq. 10 transform, E'(s_k) = sum_a A_{k,a} E'_a (with the phasing factor
+    p_a of the plan's phase centre).  Explicit sums over taps."""
     N = plan.N
     K = plan.W.shape[-1]
     h = (K - 1) // 2
@@ -628,7 +686,7 @@ def pixel_matrix(plan: Plan, c: int) -> np.ndarray:
                 jy = plan.base[c, a, 1] + dy - h - N // 2
                 m = np.mod(jx * kx + jy * ky, N)
                 A[:, a] += plan.W[c, a, dy, dx] * np.exp(2j * np.pi * m / N)
-    return A / plan.norm
+    return A / plan.norm * plan.phase[c][None, :]
 
 
 def model_image(plan: Plan, sky_lmS: np.ndarray) -> np.ndarray:

@@ -114,11 +114,11 @@ struct XengineArgs {
 };
 cudaError_t launch_xengine(const XengineArgs& a, cudaStream_t s);
 cudaError_t launch_model_vis(int n_chan, int n_ant, int n_src, const double2* ph, const double* flux,
-                             double2* vm, cudaStream_t s);
+                             float2* vm, cudaStream_t s);
 struct StefcalArgs {
   int n_chan, n_ant;
-  const double2* vis;      // [C][Na][Na]
-  const double2* vm;       // [C][Na][Na] model visibilities
+  float2* vis32;           // [C][Na][Na] scratch: the visibilities rounded to FP32
+  const float2* vm;        // [C][Na][Na] model visibilities (FP32)
   const double2* uv;       // [C][Na] antenna positions in wavelengths
   const unsigned char* flags;
   double min_baseline;     // wavelengths; shorter pairs are left out
@@ -127,7 +127,8 @@ struct StefcalArgs {
   double2* gains;          // [C][Na] in: start, out: solution
   int* iters;              // [C] iterations used, or nullptr
 };
-cudaError_t launch_stefcal(const StefcalArgs& a, cudaStream_t s);
+// Rounds vis64 into a.vis32, then solves.
+cudaError_t launch_stefcal(const StefcalArgs& a, const double2* vis64, cudaStream_t s);
 int image_rs(int rows_alloc);
 int image_rs_fused(int rows_alloc);
 

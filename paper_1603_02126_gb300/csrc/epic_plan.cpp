@@ -174,7 +174,8 @@ struct epic_plan_s {
 
   // visibility-based comparison (Sec. 4): model visibilities of the
   // configured model, formed on the first solve after epical_configure
-  DevBuf<double2> d_vm;         // [C][Na][Na]
+  DevBuf<float2> d_vm;          // [C][Na][Na] (FP32)
+  DevBuf<float2> d_vis32;       // [C][Na][Na] the solved visibilities in FP32
   DevBuf<double2> d_uv;         // [C][Na] positions in wavelengths
   DevBuf<int> d_iters;          // [C] solver iterations
   bool vm_stale = true;
@@ -1083,6 +1084,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_pph.release();
   p->d_ptap.release();
   p->d_vm.release();
+  p->d_vis32.release();
   p->d_uv.release();
   p->d_iters.release();
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -1298,8 +1300,8 @@ epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_
     return fail(EPIC_ERR_INVALID_ARG, "bad solve arguments");
   const int C = p->nc, Na = p->na;
   const size_t nv = static_cast<size_t>(C) * Na * Na;
-  if (static_cast<size_t>(2) * Na * sizeof(double2) > 200 * 1024)
-    return fail(EPIC_ERR_UNSUPPORTED, "visibility solve holds 2 x Na complex128 gains in shared memory (Na <= 6400)");
+  if (static_cast<size_t>(Na) * (2 * sizeof(double2) + sizeof(float2)) > 200 * 1024)
+    return fail(EPIC_ERR_UNSUPPORTED, "visibility solve holds the gains in shared memory (Na <= 5120)");
   if (p->vm_stale || !p->d_vm.p) {
     // phasors e_a(s) = e^{-2 pi i u_a . s} in FP64 on the host, V^M on the device
     const int ns = static_cast<int>(p->model.size() / 3);
@@ -1320,8 +1322,8 @@ epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_
     }
     DevBuf<double2> d_ph;
     DevBuf<double> d_flux;
-    cudaError_t es[] = {p->d_vm.alloc(nv), p->d_uv.alloc(uv.size()), p->d_iters.alloc(C), d_ph.alloc(ph.size()),
-                        d_flux.alloc(flux.size())};
+    cudaError_t es[] = {p->d_vm.alloc(nv), p->d_vis32.alloc(nv), p->d_uv.alloc(uv.size()), p->d_iters.alloc(C),
+                        d_ph.alloc(ph.size()), d_flux.alloc(flux.size())};
     for (cudaError_t x : es)
       if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "model visibility allocation failed");
     EPIC_CUDA(cudaMemcpyAsync(d_ph.p, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
@@ -1336,7 +1338,7 @@ epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_
   epic::StefcalArgs a{};
   a.n_chan = C;
   a.n_ant = Na;
-  a.vis = reinterpret_cast<const double2*>(d_vis);
+  a.vis32 = p->d_vis32.p;
   a.vm = p->d_vm.p;
   a.uv = p->d_uv.p;
   a.flags = p->d_flags.p;
@@ -1345,7 +1347,7 @@ epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_
   a.max_iter = max_iter;
   a.gains = reinterpret_cast<double2*>(d_gains);
   a.iters = p->d_iters.p;
-  EPIC_CUDA(epic::launch_stefcal(a, p->stream));
+  EPIC_CUDA(epic::launch_stefcal(a, reinterpret_cast<const double2*>(d_vis), p->stream));
   if (h_iters) {
     EPIC_CUDA(cudaMemcpyAsync(h_iters, p->d_iters.p, C * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     EPIC_CUDA(cudaStreamSynchronize(p->stream));

@@ -9,12 +9,15 @@
 //                For 4-bit input every product and partial sum is an integer
 //                below 2^24, so the FP32 sums are exact.
 //   model_vis    V^M[c][a][b] = sum_s S_s e_a(s) conj(e_b(s)), e_a(s) =
-//                e^{-2 pi i u_a . s}, FP64, from host phasors.
+//                e^{-2 pi i u_a . s}, FP64 from host phasors, kept in FP32.
 //   stefcal      Eq. 21 by alternating least squares with every other iterate
 //                averaged (StEFCal): one CTA per channel, one warp per antenna
-//                row at a time, FP64, iterated in the kernel until
+//                row at a time, FP32 products with FP64 reductions and
+//                update, iterated in the kernel until
 //                max_a |g_new - g| <= tol max_a |g_new| or max_iter.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "epic_internal.h"
 
@@ -113,9 +116,10 @@ __global__ void __launch_bounds__(kXThreads) xengine_kernel(const XengineArgs A)
     }
 }
 
-// V^M[c][a][b] = sum_s S_s ph[c][s][a] conj(ph[c][s][b]); one thread per pair.
+// V^M[c][a][b] = sum_s S_s ph[c][s][a] conj(ph[c][s][b]) in FP64, stored
+// rounded to FP32 for the solver; one thread per pair.
 __global__ void model_vis_kernel(int n_chan, int n_ant, int n_src, const double2* __restrict__ ph,
-                                 const double* __restrict__ flux, double2* __restrict__ vm) {
+                                 const double* __restrict__ flux, float2* __restrict__ vm) {
   const long long n = static_cast<long long>(n_chan) * n_ant * n_ant;
   const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
@@ -130,10 +134,18 @@ __global__ void model_vis_kernel(int n_chan, int n_ant, int n_src, const double2
     re += S * (pa.x * pb.x + pa.y * pb.y);
     im += S * (pa.y * pb.x - pa.x * pb.y);
   }
-  vm[i] = make_double2(re, im);
+  vm[i] = make_float2(static_cast<float>(re), static_cast<float>(im));
 }
 
-constexpr int kSThreads = 512;
+__global__ void to_f32_kernel(long long n, const double2* __restrict__ in, float2* __restrict__ out) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    const double2 v = in[i];
+    out[i] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+  }
+}
+
+constexpr int kSThreads = 1024;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -141,48 +153,58 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One CTA per channel.  Shared memory: g, gn [Na] double2, reduction scratch.
+// One CTA per channel.  The per-pair products run in FP32 (V and V^M
+// rounded to FP32, this GPU's FP64 rate being a small fraction of its FP32
+// rate); each lane's partial sums go to FP64 for the warp reduction, the
+// division, the averaging and the convergence test.  Shared memory: g (FP64)
+// and gn [Na], g as FP32 [Na].
 __global__ void __launch_bounds__(kSThreads) stefcal_kernel(const StefcalArgs A) {
   extern __shared__ __align__(16) double2 sg[];
   double2* g = sg;
   double2* gn = sg + A.n_ant;
+  float2* gf = reinterpret_cast<float2*>(sg + 2 * A.n_ant);
   __shared__ double red_d[kSThreads / 32], red_m[kSThreads / 32];
   __shared__ int done;
   const int c = blockIdx.x, Na = A.n_ant;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kSThreads / 32;
-  const double2* V = A.vis + static_cast<size_t>(c) * Na * Na;
-  const double2* VM = A.vm + static_cast<size_t>(c) * Na * Na;
+  const float2* V = A.vis32 + static_cast<size_t>(c) * Na * Na;
+  const float2* VM = A.vm + static_cast<size_t>(c) * Na * Na;
   const double2* uv = A.uv + static_cast<size_t>(c) * Na;
   const double mb2 = A.min_baseline * A.min_baseline;
   double2* gio = A.gains + static_cast<size_t>(c) * Na;
-  for (int a = threadIdx.x; a < Na; a += kSThreads) g[a] = gio[a];
+  for (int a = threadIdx.x; a < Na; a += kSThreads) {
+    g[a] = gio[a];
+    gf[a] = make_float2(static_cast<float>(g[a].x), static_cast<float>(g[a].y));
+  }
   if (threadIdx.x == 0) done = 0;
   __syncthreads();
   int it = 0;
   for (; it < A.max_iter; ++it) {
     for (int a = warp; a < Na; a += nw) {
-      double nr = 0.0, ni = 0.0, den = 0.0;
+      float nr = 0.f, ni = 0.f, den = 0.f;
       if (!A.flags[a]) {
         const double2 ua = uv[a];
         for (int b = lane; b < Na; b += 32) {
           if (b == a || A.flags[b]) continue;
-          const double2 ub = uv[b];
-          const double dx = ua.x - ub.x, dy = ua.y - ub.y;
-          if (dx * dx + dy * dy < mb2) continue;
-          const double2 gb = g[b];
-          const double2 m = VM[static_cast<size_t>(a) * Na + b];
-          const double2 v = V[static_cast<size_t>(a) * Na + b];
+          if (mb2 > 0.0) {
+            const double2 ub = uv[b];
+            const double dx = ua.x - ub.x, dy = ua.y - ub.y;
+            if (dx * dx + dy * dy < mb2) continue;
+          }
+          const float2 gb = gf[b];
+          const float2 m = VM[static_cast<size_t>(a) * Na + b];
+          const float2 v = V[static_cast<size_t>(a) * Na + b];
           // z = g_b conj(VM_ab)
-          const double zr = gb.x * m.x + gb.y * m.y, zi = gb.y * m.x - gb.x * m.y;
-          nr += v.x * zr - v.y * zi;
-          ni += v.x * zi + v.y * zr;
-          den += zr * zr + zi * zi;
+          const float zr = fmaf(gb.x, m.x, gb.y * m.y), zi = fmaf(gb.y, m.x, -gb.x * m.y);
+          nr = fmaf(v.x, zr, fmaf(-v.y, zi, nr));
+          ni = fmaf(v.x, zi, fmaf(v.y, zr, ni));
+          den = fmaf(zr, zr, fmaf(zi, zi, den));
         }
       }
-      nr = warp_sum(nr);
-      ni = warp_sum(ni);
-      den = warp_sum(den);
-      if (lane == 0) gn[a] = den > 0.0 ? make_double2(nr / den, ni / den) : g[a];
+      const double snr = warp_sum(static_cast<double>(nr));
+      const double sni = warp_sum(static_cast<double>(ni));
+      const double sden = warp_sum(static_cast<double>(den));
+      if (lane == 0) gn[a] = sden > 0.0 ? make_double2(snr / sden, sni / sden) : g[a];
     }
     __syncthreads();
     double dmax = 0.0, gmax = 0.0;
@@ -212,7 +234,10 @@ __global__ void __launch_bounds__(kSThreads) stefcal_kernel(const StefcalArgs A)
       }
       done = (d <= A.tol * m) ? 1 : 0;
     }
-    for (int a = threadIdx.x; a < Na; a += kSThreads) g[a] = gn[a];
+    for (int a = threadIdx.x; a < Na; a += kSThreads) {
+      g[a] = gn[a];
+      gf[a] = make_float2(static_cast<float>(gn[a].x), static_cast<float>(gn[a].y));
+    }
     __syncthreads();
     if (done) {
       ++it;
@@ -235,14 +260,17 @@ cudaError_t launch_xengine(const XengineArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_model_vis(int n_chan, int n_ant, int n_src, const double2* ph, const double* flux,
-                             double2* vm, cudaStream_t s) {
+                             float2* vm, cudaStream_t s) {
   const long long n = static_cast<long long>(n_chan) * n_ant * n_ant;
   model_vis_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(n_chan, n_ant, n_src, ph, flux, vm);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stefcal(const StefcalArgs& a, cudaStream_t s) {
-  const size_t smem = static_cast<size_t>(2) * a.n_ant * sizeof(double2);
+cudaError_t launch_stefcal(const StefcalArgs& a, const double2* vis64, cudaStream_t s) {
+  const long long nv = static_cast<long long>(a.n_chan) * a.n_ant * a.n_ant;
+  to_f32_kernel<<<static_cast<unsigned>(std::min<long long>((nv + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      nv, vis64, a.vis32);
+  const size_t smem = static_cast<size_t>(a.n_ant) * (2 * sizeof(double2) + sizeof(float2));
   cudaError_t e = cudaFuncSetAttribute(stefcal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

@@ -90,7 +90,7 @@ def test_stefcal_matches_oracle(cut):
         go, it = O.visibility_solve(Vo[c], VM, np.ones(na, complex), flags=flags, pair_mask=mask,
                                     return_iters=True)
         assert abs(int(iters[c]) - it) <= 2, (iters[c], it)
-        assert np.max(np.abs(gs[c] - go) / np.abs(go)) < 1e-9
+        assert np.max(np.abs(gs[c] - go) / np.abs(go)) < 2e-6     # FP32 pair products
         assert np.max(np.abs(gd[c] - go) / np.abs(go)) < 1e-5
         assert gd[c, 5] == 1.0 and gs[c, 5] == 1.0
 

@@ -734,3 +734,109 @@ def test_multipixel_tracks_direction_dependent_gains():
             own = O.gain_error(O.align_phase(gd[c, :, p], dd[c, :, p]), dd[c, :, p])
             other = O.gain_error(O.align_phase(gd[c, :, p], dd[c, :, q]), dd[c, :, q])
             assert own < 0.3 * other, (c, p, own, other)
+
+
+# --------------------------------------------------------------------------
+# bandpass model fitted across channels (Sec. 6, "Fitting gain models")
+# --------------------------------------------------------------------------
+def test_fit_bandpass_recovers_polynomial_gains_exactly():
+    """Gains that are exactly a degree-2 amplitude and a degree-3 phase
+    polynomial in frequency (phase wrapping several times across the band)
+    are returned unchanged by the fit of those degrees; channels outside the
+    band and a flagged antenna are untouched."""
+    rng = np.random.default_rng(70)
+    C, Na = 24, 7
+    freqs = np.linspace(40e6, 80e6, C)
+    g = synth.true_gains(C, Na, rng)
+    c_lo, c_hi = 3, 21
+    x = O.bandpass_x(freqs, c_lo, c_hi)
+    assert np.isclose(x[0], -1) and np.isclose(x[-1], 1)
+    want = g.copy()
+    for a in range(Na):
+        amp = 1.0 + 0.1 * a + 0.2 * x - 0.05 * x ** 2
+        ph = 0.3 * a + 9.0 * x + 1.5 * x ** 2 - 2.0 * x ** 3       # > 2 pi across the band
+        want[c_lo:c_hi, a] = amp * np.exp(1j * ph)
+    flags = np.zeros(Na, bool)
+    flags[4] = True
+    got = O.fit_bandpass(want, freqs, c_lo, c_hi, 2, 3, flags)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+    noisy = want.copy()
+    noisy[c_lo:c_hi] *= 1 + 0.05 * rng.normal(size=(c_hi - c_lo, Na))
+    fit = O.fit_bandpass(noisy, freqs, c_lo, c_hi, 2, 3, flags)
+    assert np.array_equal(fit[:c_lo], noisy[:c_lo]) and np.array_equal(fit[c_hi:], noisy[c_hi:])
+    assert np.array_equal(fit[:, 4], noisy[:, 4])
+
+
+def test_fit_bandpass_degree_zero_is_mean_amplitude_and_phase():
+    """Degree 0 in both: every channel of the band gets the mean amplitude and
+    the mean unwrapped phase of the antenna's solutions there."""
+    rng = np.random.default_rng(71)
+    C, Na = 10, 5
+    freqs = np.linspace(50e6, 60e6, C)
+    g = synth.true_gains(C, Na, rng)
+    fit = O.fit_bandpass(g, freqs, 2, 9, 0, 0)
+    for a in range(Na):
+        band = g[2:9, a]
+        want = np.mean(np.abs(band)) * np.exp(1j * np.mean(np.unwrap(np.angle(band))))
+        assert np.allclose(fit[2:9, a], want, rtol=1e-13, atol=0)
+
+
+def test_fit_bandpass_reduces_gain_noise():
+    """Noisy per-channel solutions around a smooth bandpass (the situation
+    Sec. 6 describes): the fitted gains lie closer to the truth."""
+    rng = np.random.default_rng(72)
+    C, Na = 64, 32
+    freqs = np.linspace(40e6, 80e6, C)
+    x = O.bandpass_x(freqs, 0, C)
+    true = np.empty((C, Na), complex)
+    for a in range(Na):
+        c0, c1 = rng.normal(size=2)
+        true[:, a] = (1.0 + 0.1 * c0 * x) * np.exp(1j * (rng.uniform(-np.pi, np.pi) + 3.0 * c1 * x))
+    noisy = true * (1 + 0.1 * (rng.normal(size=(C, Na)) + 1j * rng.normal(size=(C, Na))))
+    fit = O.fit_bandpass(noisy, freqs, 0, C, 2, 2)
+    assert O.gain_error(fit, true) < 0.4 * O.gain_error(noisy, true)
+
+
+# --------------------------------------------------------------------------
+# phasing off zenith (Sec. 2.1 footnote)
+# --------------------------------------------------------------------------
+def test_phased_image_is_the_shifted_sky():
+    """A planar array phased to s0 images a sky exactly as the unphased array
+    images that sky moved by -s0 (same source signals, no noise), and the
+    calibration response of the phase-centre pixel is p_a / Na."""
+    rng = np.random.default_rng(80)
+    Na, N, T = 20, 32, 40
+    ant = synth.layout_disc(Na, 12.0, rng, 1.0)
+    f = [50e6, 66e6]
+    s0 = (0.3125, -0.21875)
+    sky = np.array([[0.35, -0.2, 3.0], [0.1, 0.05, 1.0], [0.5, -0.4, 2.0]])
+    g = synth.true_gains(2, Na, rng)
+    E = synth.voltages(ant, f, g, sky, T, 0.0, np.random.default_rng(5))
+    shifted = sky - np.array([s0[0], s0[1], 0.0])
+    Es = synth.voltages(ant, f, g, shifted, T, 0.0, np.random.default_rng(5))
+    pp = O.Plan(ant, f, N, 0.5, phase_lm=s0, cal_lm=s0)
+    p0 = O.Plan(ant, f, N, 0.5)
+    img, _ = O.image_interval(pp, E, g)
+    ref, _ = O.image_interval(p0, Es, g)
+    assert np.max(np.abs(img - ref)) <= 1e-12 * np.max(ref)
+    assert pp.k0 == (N // 2, N // 2)
+    assert np.allclose(pp.A0, pp.phase / Na, rtol=1e-13, atol=0)
+
+
+def test_phased_epical_converges_off_zenith():
+    """Calibrator at 40 degrees from zenith, array phased to it: noise-free
+    EPICal from g = 1 converges to the true gains (global phase)."""
+    rng = np.random.default_rng(81)
+    Na = 14
+    ant = synth.layout_disc(Na, 10.0, rng, 1.0)
+    s0 = (0.5, 0.375)                        # sin(theta) ~ 0.63
+    sky = np.array([[s0[0], s0[1], 3.0]])
+    g = synth.true_gains(1, Na, rng)
+    E = synth.voltages(ant, [52e6], g, sky, 32, 0.0, rng, unit_modulus=True)
+    plan = O.Plan(ant, [52e6], 16, 0.5, cal_lm=s0, model_lmS=sky, phase_lm=s0)
+    gc = np.ones((1, Na), complex)
+    for _ in range(80):
+        gc, *_ = O.epical_interval(plan, E, gc, 0.35, with_image=False)
+    ga = O.align_phase(gc[0], g[0])
+    assert np.max(np.abs(ga - g[0]) / np.abs(g[0])) < 1e-10
+
