@@ -292,7 +292,8 @@ epic_status epic_visibilities(epic_plan_t plan, const void* d_volt, long long n_
  * it.  The pair products run in FP32 (V and V^M rounded to FP32; the plan
  * holds 2 x C x Na x Na complex64 for them), the sums over antennas, the
  * update, the averaging and the stopping test in FP64, so the solution
- * agrees with an FP64 solve to about 1e-6.  d_vis: device [C][Na][Na]
+ * agrees with an FP64 solve to about 1e-6; the stopping tolerance used is
+ * max(tol, 1e-6).  d_vis: device [C][Na][Na]
  * complex128 (as from epic_visibilities).  d_gains: device [C][Na]
  * complex128, the start on input and the solution on output; flagged
  * antennas and antennas with no usable pair keep their start value.
@@ -313,6 +314,34 @@ epic_status epic_visibility_solve(epic_plan_t plan, const double* d_vis, double*
  * Asynchronous on the plan stream.
  * Errors: INVALID_ARG (NULL plan, unless 0 <= c_lo < c_hi <= C), CUDA. */
 epic_status epical_average_channels(epic_plan_t plan, int c_lo, int c_hi);
+
+/* Gain model across frequency (Sec. 6, "Fitting gain models": a low-order
+ * polynomial in amplitude and in phase over a band of channels, a step
+ * beyond the constant-across-band average of epical_average_channels).
+ * For every unflagged antenna, the amplitudes |g| and the phases arg g of
+ * channels c_lo <= c < c_hi (phases unwrapped along the band from c_lo, each
+ * step taken within pi) are fitted by least squares with polynomials of
+ * degrees deg_amp and deg_phase in x, the channel frequency mapped linearly
+ * onto [-1, 1] over the band; the band's gains (and 1/g) are replaced by
+ * A(x) e^{i Phi(x)}.  An antenna with a zero or non-finite gain in the band
+ * is left as it is.  Call after epical_update.  FP64.  Synchronous.
+ * Errors: INVALID_ARG (band, or degrees outside 0..7 or not below the
+ * number of channels in the band), CUDA. */
+epic_status epical_fit_bandpass(epic_plan_t plan, int c_lo, int c_hi, int deg_amp, int deg_phase);
+
+/* Phase centre away from zenith (Sec. 2.1 footnote: a phase applied to the
+ * electric fields as one phases visibilities).  Every voltage of antenna a
+ * in channel c is multiplied by p_a = e^{+2 pi i u_a . s0}, s0 = (l0, m0),
+ * u_a = r_a f_c / c, together with the gain correction (the stored
+ * multiplier becomes p_a / g_a), so that the image is centred on s0:
+ * pixel kx holds l = l0 + (kx - N/2)/(N du), and likewise for m.  EPICal
+ * uses the phased responses (A_{0,a} p_a) and takes calibrator and
+ * calibration-pixel directions relative to s0; the gains keep their Eq. 7
+ * meaning and the gradient of epic_image_backward stays with respect to g.
+ * (0, 0) returns to zenith.  EPICal must be configured again afterwards
+ * (the call resets it).  Synchronous.
+ * Errors: INVALID_ARG (l0^2 + m0^2 >= 1), OOM, CUDA. */
+epic_status epic_set_phase_centre(epic_plan_t plan, double l0, double m0);
 
 /* Wait for the plan's stream.  *n_held (may be NULL) receives the number
  * of held (antenna, channel) gains since the previous sync; the call

@@ -29,7 +29,8 @@ EXPORTS = [
     "epic_plan_get_grid_table", "epic_unpack_ci4", "epic_last_error",
     "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
     "epic_graph_launch", "epic_measure_fma_peak", "epical_configure_pixels",
-    "epical_get_direction_gains", "epic_visibilities", "epic_visibility_solve",
+    "epical_get_direction_gains", "epic_visibilities", "epic_visibility_solve", "epical_fit_bandpass",
+    "epic_set_phase_centre",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -121,6 +122,8 @@ def load(path: str | None = None) -> ct.CDLL:
         "epical_get_direction_gains": [P, c_dp],
         "epic_visibilities": [P, P, ct.c_longlong, P, ct.c_int],
         "epic_visibility_solve": [P, P, P, ct.c_int, ct.c_double, ct.c_double, c_ip],
+        "epical_fit_bandpass": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_int],
+        "epic_set_phase_centre": [P, ct.c_double, ct.c_double],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -278,6 +278,15 @@ class Plan:
                                                 float(tol), float(min_baseline), it.ctypes.data_as(B.c_ip)))
         return it
 
+    def fit_bandpass(self, c_lo, c_hi, deg_amp, deg_phase):
+        """Polynomial gain model in amplitude and phase across channels
+        c_lo..c_hi-1 (Sec. 6); after update."""
+        B.check(self._lib.epical_fit_bandpass(self.handle, int(c_lo), int(c_hi), int(deg_amp), int(deg_phase)))
+
+    def set_phase_centre(self, l0, m0):
+        """Phase the array to (l0, m0) (Sec. 2.1 footnote); resets EPICal."""
+        B.check(self._lib.epic_set_phase_centre(self.handle, float(l0), float(m0)))
+
     def update(self, gains_out=None, status=None):
         torch = _torch()
         B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),

@@ -99,6 +99,7 @@ struct MultiUpdateArgs {
   double2* gout;           // [C][Na] or nullptr
   int* status;             // [C][Na] or nullptr
   int* held_count;
+  const double2* phase;    // [C][Na] phasing factors, or nullptr
 };
 cudaError_t launch_update_multi(const MultiUpdateArgs& a, cudaStream_t s);
 
@@ -172,6 +173,7 @@ struct UpdateArgs {
   double2* gout;           // [C][Na] or nullptr
   int* status;             // [C][Na] or nullptr
   int* held_count;         // device counter
+  const double2* phase;    // [C][Na] phasing to the phase centre (w = p / g), or nullptr
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 
@@ -200,12 +202,19 @@ struct AdjointArgs {
   size_t smem;
 };
 cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s);
+// phase: [C][Na] phasing factors p (the multiplier is w = p / g), or nullptr.
 cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
-                                    const unsigned char* flags, double2* out, cudaStream_t s);
-cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s);
+                                    const double2* phase, const unsigned char* flags, double2* out,
+                                    cudaStream_t s);
+cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, const double2* phase,
+                             cudaStream_t s);
 // Complex mean of the gains of channels [c_lo, c_hi) per unflagged antenna.
 cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigned char* flags, double2* gain,
-                                    float2* wgain, cudaStream_t s);
+                                    float2* wgain, const double2* phase, cudaStream_t s);
+// Polynomial gain model across channels [c_lo, c_hi); x: device [c_hi - c_lo] abscissa.
+cudaError_t launch_fit_bandpass(int n_ant, int c_lo, int c_hi, int deg_amp, int deg_phase, const double* x,
+                                const unsigned char* flags, double2* gain, float2* wgain, const double2* phase,
+                                cudaStream_t s);
 
 // Arguments of one batch of the plain unfused path (epic_unfused.cu).
 struct UnfusedArgs {

@@ -46,6 +46,7 @@ template <> struct Cfg<64>  { static constexpr int N1 = 8, N2 = 8,  BT = 512; };
 template <> struct Cfg<128> { static constexpr int N1 = 8, N2 = 16, BT = 512; };
 
 constexpr int kMaxAntPerThread = 4;
+constexpr double kPiD = 3.14159265358979323846;
 
 template <int N>
 struct Geo {
@@ -677,8 +678,22 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const Adjoin
 }
 
 // grad = 2 dL/dconj(g) = 2 dL/dconj(w) * (-1 / conj(g)^2); flagged -> 0.
+// Multiplier of Eq. 8 with the phasing of the plan's phase centre:
+// w = p / g (p = 1 when the plan is not phased).
+__device__ __forceinline__ float2 gain_multiplier(double gr, double gi, const double2* phase, size_t i) {
+  const double m2 = gr * gr + gi * gi;
+  double wr = gr / m2, wi = -gi / m2;
+  if (phase) {
+    const double2 q = phase[i];
+    const double xr = wr * q.x - wi * q.y, xi = wr * q.y + wi * q.x;
+    wr = xr;
+    wi = xi;
+  }
+  return make_float2(static_cast<float>(wr), static_cast<float>(wi));
+}
+
 __global__ void adjoint_finalize_kernel(int n, int n_ant, const double2* __restrict__ dldw,
-                                        const double2* __restrict__ gain,
+                                        const double2* __restrict__ gain, const double2* __restrict__ phase,
                                         const unsigned char* __restrict__ flags,
                                         double2* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -688,30 +703,36 @@ __global__ void adjoint_finalize_kernel(int n, int n_ant, const double2* __restr
     return;
   }
   const double2 g = gain[i];
-  // conj(g)^2 = (gr^2 - gi^2) - 2 i gr gi ; -1 / conj(g)^2 = -conj(g^2)/|g|^4 ... as (qr, qi)
+  // w = p / g: dw/dg = -p / g^2, so 2 dL/dconj(g) = 2 dL/dconj(w) (-conj(p) / conj(g)^2)
   const double ar = g.x * g.x - g.y * g.y, ai = -2.0 * g.x * g.y;   // conj(g)^2
   const double den = ar * ar + ai * ai;
-  const double qr = -ar / den, qi = ai / den;                       // -1 / conj(g)^2
+  double qr = -ar / den, qi = ai / den;                             // -1 / conj(g)^2
+  if (phase) {
+    const double2 q = phase[i];                                     // times conj(p)
+    const double xr = qr * q.x + qi * q.y, xi = qi * q.x - qr * q.y;
+    qr = xr;
+    qi = xi;
+  }
   const double2 d = dldw[i];
   out[i] = make_double2(2.0 * (d.x * qr - d.y * qi), 2.0 * (d.x * qi + d.y * qr));
 }
 
 // g and w = 1/g from device gains (no host round trip).
 __global__ void set_gains_kernel(int n, const double2* __restrict__ g_in, double2* __restrict__ g,
-                                 float2* __restrict__ w) {
+                                 float2* __restrict__ w, const double2* __restrict__ phase) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double2 v = g_in[i];
-  const double m2 = v.x * v.x + v.y * v.y;
   g[i] = v;
-  w[i] = make_float2(static_cast<float>(v.x / m2), static_cast<float>(-v.y / m2));
+  w[i] = gain_multiplier(v.x, v.y, phase, i);
 }
 
 // Gains constant across channels c_lo .. c_hi - 1 (Sec. 5): per unflagged
 // antenna, the complex mean of those channels' gains replaces each of them
 // (FP64; a zero or non-finite mean leaves the antenna unchanged).
 __global__ void average_channels_kernel(int n_ant, int c_lo, int c_hi, const unsigned char* __restrict__ flags,
-                                        double2* __restrict__ gain, float2* __restrict__ wgain) {
+                                        double2* __restrict__ gain, float2* __restrict__ wgain,
+                                        const double2* __restrict__ phase) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_ant || flags[a]) return;
   double sr = 0.0, si = 0.0;
@@ -725,10 +746,99 @@ __global__ void average_channels_kernel(int n_ant, int c_lo, int c_hi, const uns
   si *= inv;
   const double m2 = sr * sr + si * si;
   if (!(m2 > 0.0) || !isfinite(m2)) return;
-  const float2 w = make_float2(static_cast<float>(sr / m2), static_cast<float>(-si / m2));
   for (int c = c_lo; c < c_hi; ++c) {
-    gain[static_cast<size_t>(c) * n_ant + a] = make_double2(sr, si);
-    wgain[static_cast<size_t>(c) * n_ant + a] = w;
+    const size_t i = static_cast<size_t>(c) * n_ant + a;
+    gain[i] = make_double2(sr, si);
+    wgain[i] = gain_multiplier(sr, si, phase, i);
+  }
+}
+
+// Gain model across channels c_lo .. c_hi - 1 (Sec. 6, "Fitting gain
+// models"), one thread per unflagged antenna, FP64: amplitudes and phases
+// (unwrapped along the band, each step taken within pi) fitted by least
+// squares with polynomials of degrees da and dp in the band abscissa x[]
+// (normal equations, Gaussian elimination with partial pivoting); the
+// band's gains become A(x) e^{i Phi(x)}.  An antenna with a zero or
+// non-finite gain in the band is left as it is.
+__global__ void fit_bandpass_kernel(int n_ant, int c_lo, int c_hi, int da, int dp, const double* __restrict__ x,
+                                    const unsigned char* __restrict__ flags, double2* __restrict__ gain,
+                                    float2* __restrict__ wgain, const double2* __restrict__ phase) {
+  constexpr int kMaxDeg = 7;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_ant || flags[a]) return;
+  const int nb = c_hi - c_lo;
+  for (int c = c_lo; c < c_hi; ++c) {
+    const double2 g = gain[static_cast<size_t>(c) * n_ant + a];
+    if (!isfinite(g.x) || !isfinite(g.y) || (g.x == 0.0 && g.y == 0.0)) return;
+  }
+  double coef[2][kMaxDeg + 1];
+  for (int which = 0; which < 2; ++which) {
+    const int d = which == 0 ? da : dp;
+    const int m = d + 1;
+    double M[kMaxDeg + 1][kMaxDeg + 2];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j <= m; ++j) M[i][j] = 0.0;
+    double prev_raw = 0.0, prev = 0.0;
+    for (int k = 0; k < nb; ++k) {
+      const double2 g = gain[static_cast<size_t>(c_lo + k) * n_ant + a];
+      double y;
+      if (which == 0) {
+        y = hypot(g.x, g.y);
+      } else {
+        const double raw = atan2(g.y, g.x);
+        if (k == 0) {
+          y = raw;
+        } else {
+          const double dd = raw - prev_raw;
+          double dm = fmod(dd + kPiD, 2.0 * kPiD);
+          if (dm < 0.0) dm += 2.0 * kPiD;
+          dm -= kPiD;
+          if (dm == -kPiD && dd > 0.0) dm = kPiD;
+          y = prev + dm;
+        }
+        prev_raw = raw;
+        prev = y;
+      }
+      double xp[2 * kMaxDeg + 1];
+      xp[0] = 1.0;
+      for (int i = 1; i <= 2 * d; ++i) xp[i] = xp[i - 1] * x[k];
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) M[i][j] += xp[i + j];
+        M[i][m] += y * xp[i];
+      }
+    }
+    for (int col = 0; col < m; ++col) {            // elimination with partial pivoting
+      int piv = col;
+      for (int r = col + 1; r < m; ++r)
+        if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+      if (piv != col)
+        for (int j = 0; j <= m; ++j) {
+          const double t = M[col][j];
+          M[col][j] = M[piv][j];
+          M[piv][j] = t;
+        }
+      for (int r = col + 1; r < m; ++r) {
+        const double f = M[r][col] / M[col][col];
+        for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double v = M[i][m];
+      for (int j = i + 1; j < m; ++j) v -= M[i][j] * coef[which][j];
+      coef[which][i] = v / M[i][i];
+    }
+  }
+  for (int k = 0; k < nb; ++k) {
+    double amp = 0.0, ph = 0.0;
+    for (int i = da; i >= 0; --i) amp = amp * x[k] + coef[0][i];
+    for (int i = dp; i >= 0; --i) ph = ph * x[k] + coef[1][i];
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const double gr = amp * cs, gi = amp * sn;
+    if (!isfinite(gr) || !isfinite(gi) || (gr == 0.0 && gi == 0.0)) continue;
+    const size_t i = static_cast<size_t>(c_lo + k) * n_ant + a;
+    gain[i] = make_double2(gr, gi);
+    wgain[i] = gain_multiplier(gr, gi, phase, i);
   }
 }
 
@@ -763,8 +873,7 @@ __global__ void epical_update_kernel(const UpdateArgs A) {
   if (!held) {
     out = make_double2(nxr, nxi);
     A.gain[i] = out;
-    const double m2 = nxr * nxr + nxi * nxi;
-    A.wgain[i] = make_float2(static_cast<float>(nxr / m2), static_cast<float>(-nxi / m2));
+    A.wgain[i] = gain_multiplier(nxr, nxi, A.phase, i);
   }
   if (A.status) A.status[i] = held ? 1 : 0;
   if (held && !A.flags[a]) atomicAdd(A.held_count, 1);
@@ -871,20 +980,30 @@ cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
-                                    const unsigned char* flags, double2* out, cudaStream_t s) {
+                                    const double2* phase, const unsigned char* flags, double2* out,
+                                    cudaStream_t s) {
   const int n = n_chan * n_ant;
-  adjoint_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, n_ant, dldw, gain, flags, out);
+  adjoint_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, n_ant, dldw, gain, phase, flags, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigned char* flags, double2* gain,
-                                    float2* wgain, cudaStream_t s) {
-  average_channels_kernel<<<(n_ant + 255) / 256, 256, 0, s>>>(n_ant, c_lo, c_hi, flags, gain, wgain);
+                                    float2* wgain, const double2* phase, cudaStream_t s) {
+  average_channels_kernel<<<(n_ant + 255) / 256, 256, 0, s>>>(n_ant, c_lo, c_hi, flags, gain, wgain, phase);
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, cudaStream_t s) {
-  set_gains_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, g_in, g, w);
+cudaError_t launch_fit_bandpass(int n_ant, int c_lo, int c_hi, int deg_amp, int deg_phase, const double* x,
+                                const unsigned char* flags, double2* gain, float2* wgain, const double2* phase,
+                                cudaStream_t s) {
+  fit_bandpass_kernel<<<(n_ant + 127) / 128, 128, 0, s>>>(n_ant, c_lo, c_hi, deg_amp, deg_phase, x, flags, gain,
+                                                           wgain, phase);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_gains(int n, const double2* g_in, double2* g, float2* w, const double2* phase,
+                             cudaStream_t s) {
+  set_gains_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, g_in, g, w, phase);
   return cudaGetLastError();
 }
 

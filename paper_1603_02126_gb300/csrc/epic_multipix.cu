@@ -135,8 +135,16 @@ __global__ void update_multi_kernel(const MultiUpdateArgs A) {
   if (!held) {
     out = make_double2(nxr, nxi);
     A.gain[i] = out;
+    // w = p / g (p: phasing of the plan's phase centre, 1 if none)
     const double m2 = nxr * nxr + nxi * nxi;
-    A.wgain[i] = make_float2(static_cast<float>(nxr / m2), static_cast<float>(-nxi / m2));
+    double wr = nxr / m2, wi = -nxi / m2;
+    if (A.phase) {
+      const double2 q = A.phase[i];
+      const double xr = wr * q.x - wi * q.y, xi = wr * q.y + wi * q.x;
+      wr = xr;
+      wi = xi;
+    }
+    A.wgain[i] = make_float2(static_cast<float>(wr), static_cast<float>(wi));
   }
   if (A.status) A.status[i] = held ? 1 : 0;
   if (held && !flagged) atomicAdd(A.held_count, 1);

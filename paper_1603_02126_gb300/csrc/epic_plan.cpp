@@ -62,6 +62,22 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 }  // namespace
 
+namespace {
+// Multiplier of Eq. 8 for entry i ([C][Na] order): w = p_i / g with the
+// phasing factor p_i of the plan's phase centre (1 at zenith).
+float2 gain_multiplier_host(const std::vector<double2>& phase, size_t i, double gr, double gi) {
+  const double m2 = gr * gr + gi * gi;
+  double wr = gr / m2, wi = -gi / m2;
+  if (!phase.empty()) {
+    const double2 q = phase[i];
+    const double xr = wr * q.x - wi * q.y, xi = wr * q.y + wi * q.x;
+    wr = xr;
+    wi = xi;
+  }
+  return make_float2(static_cast<float>(wr), static_cast<float>(wi));
+}
+}  // namespace
+
 struct epic_plan_s {
   // description
   int na = 0, nc = 0, n = 0, k = 0, input = 0, kernel = 0;
@@ -179,6 +195,12 @@ struct epic_plan_s {
   DevBuf<double2> d_uv;         // [C][Na] positions in wavelengths
   DevBuf<int> d_iters;          // [C] solver iterations
   bool vm_stale = true;
+
+  // phase centre (Sec. 2.1 footnote): E_a multiplied by p_a = e^{+2 pi i u_a . s0}
+  double phase_l = 0.0, phase_m = 0.0;
+  std::vector<double2> phase;   // [C][Na] host copy (empty: zenith, not phased)
+  DevBuf<double2> d_phase;      // [C][Na] or null
+  DevBuf<double> d_bx;          // [C] bandpass fit abscissa scratch
 };
 
 namespace {
@@ -204,7 +226,8 @@ int choose_segments(int n_chan, long long n_time, int ctas, int target = 4) {
 }
 
 // A_{p,a} of channel c: exact response of image pixel (kx, ky) to antenna a
-// through its stencil, (1/Na) sum_taps W_a(j) e^{+2 pi i (j - N/2).(k - N/2)/N}.
+// through its stencil, (1/Na) sum_taps W_a(j) e^{+2 pi i (j - N/2).(k - N/2)/N},
+// times the antenna's phasing factor when the plan has a phase centre.
 void pixel_response(epic_plan_t p, int c, int kx, int ky, std::vector<std::complex<double>>& A) {
   const int Na = p->na, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
   A.assign(Na, 0.0);
@@ -225,6 +248,10 @@ void pixel_response(epic_plan_t p, int c, int kx, int ky, std::vector<std::compl
         s += wa[dy * K + dx] * std::complex<double>(std::cos(ph), std::sin(ph));
       }
     A[a] = s / static_cast<double>(Na);
+    if (!p->phase.empty()) {
+      const double2 q = p->phase[static_cast<size_t>(c) * Na + a];
+      A[a] *= std::complex<double>(q.x, q.y);
+    }
   }
 }
 
@@ -251,9 +278,12 @@ void model_denominator(epic_plan_t p, int c, const std::vector<std::complex<doub
   }
 }
 
-// Nearest pixel centre of direction (l, m): l = (k - N/2) / (N du).
+// Nearest pixel centre of direction (l, m): l - l0 = (k - N/2) / (N du), with
+// (l0, m0) the phase centre.
 bool nearest_pixel(epic_plan_t p, double l, double m, int* kx, int* ky) {
   const int N = p->n;
+  l -= p->phase_l;                         // image coordinates relative to the phase centre
+  m -= p->phase_m;
   const double kxd = std::floor(l * N * p->cell + N / 2 + 0.5);
   const double kyd = std::floor(m * N * p->cell + N / 2 + 0.5);
   if (!(kxd >= 0 && kxd < N && kyd >= 0 && kyd < N)) return false;
@@ -1085,6 +1115,8 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_ptap.release();
   p->d_vm.release();
   p->d_vis32.release();
+  p->d_phase.release();
+  p->d_bx.release();
   p->d_uv.release();
   p->d_iters.release();
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
@@ -1131,7 +1163,7 @@ epic_status epic_set_gains(epic_plan_t p, const double* gains) {
     if (!std::isfinite(re) || !std::isfinite(im) || !(m2 > 0))
       return fail(EPIC_ERR_INVALID_ARG, "gains must be finite and non-zero");
     g[i] = make_double2(re, im);
-    w[i] = make_float2(static_cast<float>(re / m2), static_cast<float>(-im / m2));
+    w[i] = gain_multiplier_host(p->phase, i, re, im);
   }
   EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
@@ -1238,8 +1270,7 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
           return fail(EPIC_ERR_INVALID_ARG, "initial gains must be finite and non-zero");
       }
       g[i] = make_double2(gr, gi);
-      const double m2 = gr * gr + gi * gi;
-      w[i] = make_float2(static_cast<float>(gr / m2), static_cast<float>(-gi / m2));
+      w[i] = gain_multiplier_host(p->phase, i, gr, gi);
     }
   }
   if (!p->d_a0.p) {
@@ -1459,7 +1490,68 @@ epic_status epical_average_channels(epic_plan_t p, int c_lo, int c_hi) {
   if (!(0 <= c_lo && c_lo < c_hi && c_hi <= p->nc))
     return fail(EPIC_ERR_INVALID_ARG, "channel band must satisfy 0 <= c_lo < c_hi <= C");
   EPIC_CUDA(epic::launch_average_channels(p->na, c_lo, c_hi, p->d_flags.p, p->d_gain.p, p->d_wgain.p,
-                                          p->stream));
+                                          p->d_phase.p, p->stream));
+  return EPIC_OK;
+}
+
+epic_status epic_set_phase_centre(epic_plan_t p, double l0, double m0) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!std::isfinite(l0) || !std::isfinite(m0) || !(l0 * l0 + m0 * m0 < 1.0))
+    return fail(EPIC_ERR_INVALID_ARG, "phase centre must satisfy l0^2 + m0^2 < 1");
+  const int C = p->nc, Na = p->na;
+  const size_t n = static_cast<size_t>(C) * Na;
+  if (l0 == 0.0 && m0 == 0.0) {
+    p->phase.clear();
+    p->d_phase.release();
+  } else {
+    p->phase.resize(n);
+    for (int c = 0; c < C; ++c)
+      for (int a = 0; a < Na; ++a) {
+        const double f = p->freq[c];
+        const double u = (p->ant[2 * a] * f) / kC, v = (p->ant[2 * a + 1] * f) / kC;
+        const double arg = 2.0 * kPi * (u * l0 + v * m0);
+        p->phase[static_cast<size_t>(c) * Na + a] = make_double2(std::cos(arg), std::sin(arg));
+      }
+    if (!p->d_phase.p && p->d_phase.alloc(n) != cudaSuccess)
+      return fail(EPIC_ERR_OOM, "phase table allocation failed");
+    EPIC_CUDA(cudaMemcpyAsync(p->d_phase.p, p->phase.data(), n * sizeof(double2), cudaMemcpyHostToDevice,
+                              p->stream));
+  }
+  p->phase_l = l0;
+  p->phase_m = m0;
+  // multipliers of the current gains with the new phasing (in place)
+  EPIC_CUDA(epic::launch_set_gains(static_cast<int>(n), p->d_gain.p, p->d_gain.p, p->d_wgain.p, p->d_phase.p,
+                                   p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));
+  // calibrator pixel and responses depend on the phase centre
+  p->cal = false;
+  p->npix = 0;
+  p->frames = 0;
+  return EPIC_OK;
+}
+
+epic_status epical_fit_bandpass(epic_plan_t p, int c_lo, int c_hi, int deg_amp, int deg_phase) {
+  if (epic_status s = check_plan(p)) return s;
+  if (!(0 <= c_lo && c_lo < c_hi && c_hi <= p->nc))
+    return fail(EPIC_ERR_INVALID_ARG, "channel band must satisfy 0 <= c_lo < c_hi <= C");
+  if (deg_amp < 0 || deg_phase < 0 || deg_amp > 7 || deg_phase > 7 || std::max(deg_amp, deg_phase) >= c_hi - c_lo)
+    return fail(EPIC_ERR_INVALID_ARG, "degrees must be 0..7 and below the number of channels in the band");
+  // abscissa: the band's frequencies mapped linearly onto [-1, 1]
+  const int nb = c_hi - c_lo;
+  double lo = p->freq[c_lo], hi = p->freq[c_lo];
+  for (int c = c_lo; c < c_hi; ++c) {
+    lo = std::min(lo, p->freq[c]);
+    hi = std::max(hi, p->freq[c]);
+  }
+  std::vector<double> x(nb, 0.0);
+  if (hi > lo)
+    for (int k = 0; k < nb; ++k) x[k] = (p->freq[c_lo + k] - 0.5 * (lo + hi)) / (0.5 * (hi - lo));
+  if (!p->d_bx.p && p->d_bx.alloc(p->nc) != cudaSuccess)
+    return fail(EPIC_ERR_OOM, "bandpass scratch allocation failed");
+  EPIC_CUDA(cudaMemcpyAsync(p->d_bx.p, x.data(), nb * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  EPIC_CUDA(epic::launch_fit_bandpass(p->na, c_lo, c_hi, deg_amp, deg_phase, p->d_bx.p, p->d_flags.p, p->d_gain.p,
+                                      p->d_wgain.p, p->d_phase.p, p->stream));
+  EPIC_CUDA(cudaStreamSynchronize(p->stream));     // x is host memory of this call
   return EPIC_OK;
 }
 
@@ -1487,6 +1579,7 @@ epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
     m.gout = reinterpret_cast<double2*>(d_gains_out);
     m.status = d_status;
     m.held_count = p->d_held.p;
+    m.phase = p->d_phase.p;
     EPIC_CUDA(epic::launch_update_multi(m, p->stream));
     p->frames = 0;
     p->iteration += 1;
@@ -1508,6 +1601,7 @@ epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
   u.gout = reinterpret_cast<double2*>(d_gains_out);
   u.status = d_status;
   u.held_count = p->d_held.p;
+  u.phase = p->d_phase.p;
   EPIC_CUDA(epic::launch_update(u, p->stream));
   p->frames = 0;
   p->iteration += 1;
@@ -1597,10 +1691,7 @@ epic_status epical_set_state(epic_plan_t p, const void* buf, size_t bytes) {
   std::vector<double2> g(n);
   std::memcpy(g.data(), i, n * sizeof(double2));
   std::vector<float2> w(n);
-  for (size_t k = 0; k < n; ++k) {
-    const double m2 = g[k].x * g[k].x + g[k].y * g[k].y;
-    w[k] = make_float2(static_cast<float>(g[k].x / m2), static_cast<float>(-g[k].y / m2));
-  }
+  for (size_t k = 0; k < n; ++k) w[k] = gain_multiplier_host(p->phase, k, g[k].x, g[k].y);
   EPIC_CUDA(cudaMemcpyAsync(p->d_gain.p, g.data(), n * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_wgain.p, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
   EPIC_CUDA(cudaMemcpyAsync(p->d_kacc.p, i + n * sizeof(double2), n * sizeof(double2),
@@ -1773,7 +1864,7 @@ epic_status epic_set_gains_device(epic_plan_t p, const double* d_gains) {
   if (epic_status s = check_plan(p)) return s;
   if (!d_gains) return fail(EPIC_ERR_INVALID_ARG, "d_gains is NULL");
   EPIC_CUDA(epic::launch_set_gains(p->nc * p->na, reinterpret_cast<const double2*>(d_gains), p->d_gain.p,
-                                   p->d_wgain.p, p->stream));
+                                   p->d_wgain.p, p->d_phase.p, p->stream));
   return EPIC_OK;
 }
 
@@ -1817,7 +1908,7 @@ epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_t
   a.gbase = p->d_ugbase.p;
   a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs, p->na);
   EPIC_CUDA(epic::launch_adjoint(p->n, a, p->stream));
-  EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_flags.p,
+  EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_phase.p, p->d_flags.p,
                                           reinterpret_cast<double2*>(d_grad_g), p->stream));
   return EPIC_OK;
 }

@@ -146,6 +146,7 @@ __global__ void to_f32_kernel(long long n, const double2* __restrict__ in, float
 }
 
 constexpr int kSThreads = 1024;
+constexpr double kStefcalMinTol = 1e-6;   // smallest stopping tolerance with FP32 pair products
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(kSThreads) stefcal_kernel(const StefcalArgs A)
         d = fmax(d, red_d[w]);
         m = fmax(m, red_m[w]);
       }
-      done = (d <= A.tol * m) ? 1 : 0;
+      // FP32 pair products: changes below ~1e-6 are rounding, not progress
+      done = (d <= fmax(A.tol, kStefcalMinTol) * m) ? 1 : 0;
     }
     for (int a = threadIdx.x; a < Na; a += kSThreads) {
       g[a] = gn[a];
