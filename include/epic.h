@@ -113,6 +113,8 @@ typedef struct {
   int cols_target;             /* UNFUSED: column-FFT units per SM aimed for */
   double ms_default, ms_best;  /* epic_image time before / after tuning */
   int candidates;              /* launch shapes timed */
+  int row_table;               /* UNFUSED FP32 row kernel: gather table -1 auto, 0 L1, 1 shared memory */
+  int row_frames;              /* UNFUSED FP32 row kernel: frames per step (1 or 2) */
 } epic_tune_result;
 
 /* Build the gridding tables of Eq. 9 for every (channel, antenna): the
@@ -184,8 +186,9 @@ epic_status epic_image_host_static(epic_plan_t plan, const void* h_volt, long lo
 /* Batching form, autotuner: times candidate launch shapes of epic_image on
  * this batch (FUSED: work units per CTA, i.e. the time-segment length of a
  * persistent CTA's work unit; UNFUSED: time samples per batch and
- * column-FFT work units per SM), keeps the fastest in the plan and reports
- * it in *out (may be NULL).  d_image is overwritten; EPICal sums are left
+ * column-FFT work units per SM, then for FP32 the row kernel's variant:
+ * gather table in shared memory or read through L1, one or two frames per
+ * step), keeps the fastest in the plan and reports it in *out (may be NULL).  d_image is overwritten; EPICal sums are left
  * untouched.  Synchronous.  The paper has no counterpart (run-time tuning
  * of this implementation). */
 epic_status epic_autotune(epic_plan_t plan, const void* d_volt, long long n_time, double* d_image,

@@ -70,7 +70,7 @@ class TuneResult(ct.Structure):
     _fields_ = [
         ("path", ct.c_int), ("units_target", ct.c_int), ("batch_time", ct.c_int),
         ("cols_target", ct.c_int), ("ms_default", ct.c_double), ("ms_best", ct.c_double),
-        ("candidates", ct.c_int),
+        ("candidates", ct.c_int), ("row_table", ct.c_int), ("row_frames", ct.c_int),
     ]
 
 

@@ -241,6 +241,14 @@ struct UnfusedArgs {
   double2* kacc;
   double* pacc;
   int cols_target;         // column-FFT work units per SM to aim for
+  // plain FP32 path (window coordinates): the gather tables above hold
+  // window columns; the calibrator pixel takes the window phase pixph
+  const float2* pixph;     // [C] (-1)^(k0x+k0y) e^{2 pi i (x0 k0x + y0 k0y)/N}
+  int max_cols;            // widest channel's occupied columns
+  int gmax;                // most gather entries of one channel
+  int* err;                // device flag: a bounded wait timed out
+  int row_table;           // row kernel's gather table: -1 auto, 0 L1, 1 shared memory
+  int row_frames;          // row kernel's frames per step, 1 or 2
 };
 bool unfused_supported(int n);
 // Lanes per row FFT (N1) of the unfused kernels: absolute column x is gather

@@ -119,6 +119,7 @@ struct epic_plan_s {
   DevBuf<float2> d_pixph;       // [C] calibrator-pixel phase in window coordinates
   std::vector<int> x0, cols;    // [C] first occupied column, occupied columns
   int rs_fused = 0;
+  int gmax = 0;                 // most gather entries of one channel (window tables)
   DevBuf<float2> d_twid;        // [N]
   DevBuf<unsigned char> d_flags;  // [Na]
 
@@ -156,6 +157,8 @@ struct epic_plan_s {
   int tune_units = 4;           // fused: work units per CTA to aim for
   int tune_nt = 0;              // unfused: time samples per batch (0 = budget)
   int tune_cols = 4;            // unfused: column units per SM to aim for
+  int tune_row_table = -1;      // unfused row kernel: gather table -1 auto, 0 L1, 1 shared memory
+  int tune_row_frames = 2;      // unfused row kernel: frames per step
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
 
@@ -319,7 +322,64 @@ epic_status ensure_ptap(epic_plan_t p, long long n_time) {
   return EPIC_OK;
 }
 
-// Arguments of one fused launch over a device batch.
+// Gridding of Eq. 9 inverted into per-lane gather lists.  The grid of
+// channel c holds its occupied rows (window row r = y - y0[c]); an N-point
+// row FFT runs on N1 lanes, lane n1 holding the columns x = n1 + N1 j.  For
+// every lane (r, n1) the list holds the taps (antenna, folded weight) that
+// land on its columns, grouped by j, with the group lengths as bytes
+// (ceil(N2 / 16) 16-byte words per lane).  window: columns relative to the
+// first occupied column x0[c] (a phase of every image pixel, removed where
+// a pixel value is needed), else absolute.  ofs [C][rows_alloc][N1] is the
+// lane's first entry relative to the channel's first (base [C + 1]).
+epic_status build_gather(epic_plan_t p, const std::vector<float>& wts, int N1, bool window, std::vector<int>& ofs,
+                         std::vector<uint4>& cnt, std::vector<uint2>& ent, std::vector<int>& base) {
+  const int C = p->nc, Na = p->na, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
+  const int N2 = N / N1, CW = (N2 + 15) / 16;
+  const int RA = p->rows_alloc;
+  ofs.assign(static_cast<size_t>(C) * RA * N1, 0);
+  cnt.assign(static_cast<size_t>(C) * RA * N1 * CW, make_uint4(0, 0, 0, 0));
+  base.assign(static_cast<size_t>(C) + 1, 0);
+  ent.clear();
+  std::vector<std::vector<std::pair<int, float>>> bucket(static_cast<size_t>(RA) * N1 * N2);
+  for (int c = 0; c < C; ++c) {
+    base[c] = static_cast<int>(ent.size());
+    for (auto& l : bucket) l.clear();
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      const int r0 = p->base[ob + 1] - h - p->y0[c];
+      const int xa = p->base[ob] - h - (window ? p->x0[c] : 0);
+      const float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
+      for (int dy = 0; dy < K; ++dy)
+        for (int dx = 0; dx < K; ++dx) {
+          const float w = wf[dy * K + dx];
+          if (w == 0.0f) continue;
+          const int x = xa + dx;
+          bucket[(static_cast<size_t>(r0 + dy) * N1 + x % N1) * N2 + x / N1].emplace_back(a, w);
+        }
+    }
+    for (int li = 0; li < RA * N1; ++li) {
+      ofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(ent.size()) - base[c];
+      unsigned char cb[32] = {0};
+      for (int j = 0; j < N2; ++j) {
+        const auto& l = bucket[static_cast<size_t>(li) * N2 + j];
+        if (l.size() > 255) return fail(EPIC_ERR_UNSUPPORTED, "more than 255 gridding taps on one grid cell");
+        cb[j] = static_cast<unsigned char>(l.size());
+        for (const auto& en : l) {
+          uint2 q;
+          q.x = static_cast<unsigned>(en.first);
+          std::memcpy(&q.y, &en.second, sizeof(float));
+          ent.push_back(q);
+        }
+      }
+      std::memcpy(&cnt[(static_cast<size_t>(c) * RA * N1 + li) * CW], cb, sizeof(uint4) * CW);
+    }
+  }
+  base[C] = static_cast<int>(ent.size());
+  return EPIC_OK;
+}
+
+// Arguments of one fused launch over a device batch.// Arguments of one fused launch over a device batch.
 epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
                            double img_scale) {
   epic::ImageArgs a{};
@@ -438,12 +498,18 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   const size_t cap = static_cast<size_t>(p->ws_time) * C;
   a.spec = p->d_ws.p;
   a.pix = a.spec + cap * N * p->rs;
-  a.gofs = p->d_ugofs.p;
-  a.gcnt = p->d_ugcnt.p;
-  a.gent = p->d_ugent.p;
-  a.gbase = p->d_ugbase.p;
+  a.gofs = p->d_gofs.p;                    // window-column gather tables
+  a.gcnt = p->d_gcnt.p;
+  a.gent = p->d_gent.p;
+  a.gbase = p->d_gbase.p;
   a.rows_alloc = p->rows_alloc;
   a.rs = p->rs;
+  a.pixph = p->d_pixph.p;
+  a.max_cols = *std::max_element(p->cols.begin(), p->cols.end());
+  a.gmax = p->gmax;
+  a.err = p->d_err.p;
+  a.row_table = p->tune_row_table;
+  a.row_frames = p->tune_row_frames;
   a.image = d_image;
   a.img_scale = 1.0 / static_cast<double>(n_time);
   a.do_cal = p->cal ? 1 : 0;
@@ -893,111 +959,27 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       const int bx = p->base[ob], by = p->base[ob + 1];
       cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
     }
-  // fused path: per FFT lane (window row r, lane n1 = x mod N1) the taps on
-  // its columns x = n1 + N1 j, grouped by j; the group lengths as bytes
-  std::vector<int> gofs, gbase;
-  std::vector<uint4> gcnt;
-  std::vector<uint2> gent;
-  if (p->path == EPIC_PATH_FUSED) {
-    const int N1 = epic::image_fft_lanes(N);
-    const int N2 = N / N1;
-    const int RA = p->rows_alloc;
-    gofs.assign(static_cast<size_t>(C) * RA * N1, 0);
-    gcnt.assign(static_cast<size_t>(C) * RA * N1, make_uint4(0, 0, 0, 0));
-    std::vector<std::vector<std::pair<int, float>>> bucket(static_cast<size_t>(RA) * N1 * N2);
-    gbase.assign(static_cast<size_t>(C) + 1, 0);
-    for (int c = 0; c < C; ++c) {
-      gbase[c] = static_cast<int>(gent.size());
-      for (auto& l : bucket) l.clear();
-      for (int a = 0; a < Na; ++a) {
-        if (p->flags[a]) continue;
-        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
-        const int r0 = p->base[ob + 1] - h - p->y0[c], x0w = p->base[ob] - h - p->x0[c];
-        const float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
-        for (int dy = 0; dy < K; ++dy)
-          for (int dx = 0; dx < K; ++dx) {
-            const float w = wf[dy * K + dx];
-            if (w == 0.0f) continue;
-            const int x = x0w + dx;
-            bucket[(static_cast<size_t>(r0 + dy) * N1 + x % N1) * N2 + x / N1].emplace_back(a, w);
-          }
-      }
-      for (int li = 0; li < RA * N1; ++li) {
-        gofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(gent.size()) - gbase[c];
-        unsigned char cnt[16] = {0};
-        for (int j = 0; j < N2; ++j) {
-          const auto& l = bucket[static_cast<size_t>(li) * N2 + j];
-          if (l.size() > 255) {
-            epic_plan_destroy(p);
-            return fail(EPIC_ERR_UNSUPPORTED, "fused path: more than 255 gridding taps on one grid cell");
-          }
-          cnt[j] = static_cast<unsigned char>(l.size());
-          for (const auto& en : l) {
-            uint2 q;
-            q.x = static_cast<unsigned>(en.first);
-            std::memcpy(&q.y, &en.second, sizeof(float));
-            gent.push_back(q);
-          }
-        }
-        uint4 cw;
-        std::memcpy(&cw, cnt, sizeof(cw));
-        gcnt[static_cast<size_t>(c) * RA * N1 + li] = cw;
-      }
+  // gridding gather tables (see build_gather): the fused kernel and the
+  // plain unfused FP32 path grid in window columns, the fused path's adjoint
+  // and the reduced-precision row kernel in absolute columns
+  std::vector<int> gofs, gbase, ugofs, ugbase;
+  std::vector<uint4> gcnt, ugcnt;
+  std::vector<uint2> gent, ugent;
+  const bool unfused_fp32 = p->path == EPIC_PATH_UNFUSED && p->precision == EPIC_PREC_FP32;
+  if (p->path == EPIC_PATH_FUSED || unfused_fp32) {
+    const int n1 = p->path == EPIC_PATH_FUSED ? epic::image_fft_lanes(N) : epic::unfused_fft_lanes(N);
+    if (epic_status st = build_gather(p, wts, n1, true, gofs, gcnt, gent, gbase)) {
+      epic_plan_destroy(p);
+      return st;
     }
-    gbase[C] = static_cast<int>(gent.size());
+    for (int c = 0; c < C; ++c) p->gmax = std::max(p->gmax, gbase[c + 1] - gbase[c]);
   }
-  // unfused path and the fused path's adjoint: per row-FFT lane (window row,
-  // lane n1 = x mod N1, x the absolute column) the taps on its columns
-  // x = n1 + N1 j, grouped by j; the group lengths as bytes, ceil(N2 / 16)
-  // 16-byte words per lane
-  std::vector<int> ugofs, ugbase;
-  std::vector<uint4> ugcnt;
-  std::vector<uint2> ugent;
-  if (p->path == EPIC_PATH_UNFUSED || p->path == EPIC_PATH_FUSED) {
-    const int N1 = p->path == EPIC_PATH_UNFUSED ? epic::unfused_fft_lanes(N) : epic::image_fft_lanes(N);
-    const int N2 = N / N1, CW = (N2 + 15) / 16;
-    const int RA = p->rows_alloc;
-    ugofs.assign(static_cast<size_t>(C) * RA * N1, 0);
-    ugcnt.assign(static_cast<size_t>(C) * RA * N1 * CW, make_uint4(0, 0, 0, 0));
-    ugbase.assign(static_cast<size_t>(C) + 1, 0);
-    std::vector<std::vector<std::pair<int, float>>> bucket(static_cast<size_t>(RA) * N1 * N2);
-    for (int c = 0; c < C; ++c) {
-      ugbase[c] = static_cast<int>(ugent.size());
-      for (auto& l : bucket) l.clear();
-      for (int a = 0; a < Na; ++a) {
-        if (p->flags[a]) continue;
-        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
-        const int r0 = p->base[ob + 1] - h - p->y0[c], xa = p->base[ob] - h;
-        const float* wf = &wts[(static_cast<size_t>(c) * Na + a) * KK];
-        for (int dy = 0; dy < K; ++dy)
-          for (int dx = 0; dx < K; ++dx) {
-            const float w = wf[dy * K + dx];
-            if (w == 0.0f) continue;
-            const int x = xa + dx;
-            bucket[(static_cast<size_t>(r0 + dy) * N1 + x % N1) * N2 + x / N1].emplace_back(a, w);
-          }
-      }
-      for (int li = 0; li < RA * N1; ++li) {
-        ugofs[static_cast<size_t>(c) * RA * N1 + li] = static_cast<int>(ugent.size()) - ugbase[c];
-        unsigned char cnt[32] = {0};
-        for (int j = 0; j < N2; ++j) {
-          const auto& l = bucket[static_cast<size_t>(li) * N2 + j];
-          if (l.size() > 255) {
-            epic_plan_destroy(p);
-            return fail(EPIC_ERR_UNSUPPORTED, "unfused path: more than 255 gridding taps on one grid cell");
-          }
-          cnt[j] = static_cast<unsigned char>(l.size());
-          for (const auto& en : l) {
-            uint2 q;
-            q.x = static_cast<unsigned>(en.first);
-            std::memcpy(&q.y, &en.second, sizeof(float));
-            ugent.push_back(q);
-          }
-        }
-        std::memcpy(&ugcnt[(static_cast<size_t>(c) * RA * N1 + li) * CW], cnt, sizeof(uint4) * CW);
-      }
+  if (p->path == EPIC_PATH_FUSED || (p->path == EPIC_PATH_UNFUSED && !unfused_fp32)) {
+    const int n1 = p->path == EPIC_PATH_UNFUSED ? epic::unfused_fft_lanes(N) : epic::image_fft_lanes(N);
+    if (epic_status st = build_gather(p, wts, n1, false, ugofs, ugcnt, ugent, ugbase)) {
+      epic_plan_destroy(p);
+      return st;
     }
-    ugbase[C] = static_cast<int>(ugent.size());
   }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
   // cluster path: stencil (top row, first column) in window coordinates,
@@ -1618,7 +1600,7 @@ epic_status epic_plan_sync(epic_plan_t p, int* n_held) {
   if (n_held) *n_held = held;
   if (err) {
     EPIC_CUDA(cudaMemset(p->d_err.p, 0, sizeof(int)));
-    return fail(EPIC_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core kernel)");
+    return fail(EPIC_ERR_TIMEOUT, "a bounded device wait timed out (a TMA-fed kernel gave up)");
   }
   if (held > 0) return fail(EPIC_ERR_NUMERIC, std::to_string(held) + " gains held by the EPICal update");
   return EPIC_OK;
@@ -1795,6 +1777,27 @@ epic_status epic_autotune(epic_plan_t p, const void* d_volt, long long n_time, d
     if (r.batch_time == budget_nt && def_nt == 0) r.batch_time = 0;
     p->tune_nt = r.batch_time;
     p->tune_cols = r.cols_target;
+    // then the row kernel's variant: gather table in L1 or shared memory,
+    // one or two frames per step
+    r.row_table = p->tune_row_table;
+    r.row_frames = p->tune_row_frames;
+    if (p->precision == EPIC_PREC_FP32)
+      for (int tb : {0, 1})
+        for (int rf : {1, 2}) {
+          if (st != EPIC_OK) break;
+          p->tune_row_table = tb;
+          p->tune_row_frames = rf;
+          double ms = 0;
+          st = time_image(p, d_volt, n_time, d_image, reps, &ms);
+          ++r.candidates;
+          if (st == EPIC_OK && ms < best) {
+            best = ms;
+            r.row_table = tb;
+            r.row_frames = rf;
+          }
+        }
+    p->tune_row_table = r.row_table;
+    p->tune_row_frames = r.row_frames;
   }
   p->cal = cal;
   p->frames = frames;

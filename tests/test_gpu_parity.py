@@ -137,12 +137,14 @@ def test_image_sizes_flags_supports(n, na, k):
     assert _rel(img, ref) <= IMG_TOL
 
 
+@pytest.mark.parametrize("path", ["fused", "unfused"])
 @pytest.mark.parametrize("n,na,diam", [(32, 40, 57.0), (64, 60, 117.0), (128, 120, 217.0)])
-def test_fused_full_window_matches_oracle(n, na, diam):
+def test_full_window_matches_oracle(n, na, diam, path):
     """An array whose occupied grid window spans more than N/2 cells in both
-    channels, so that the fused kernel takes its unpruned-FFT variant (every
-    lane holds N2 non-zero inputs).  Image and one EPICal interval with an
-    off-centre calibrator against the oracle; T odd (a one-frame last step)."""
+    channels, so that the fused kernel and the plain path's row and column
+    kernels take their unpruned-FFT variants (every lane holds N2 non-zero
+    inputs).  Image and one EPICal interval with an off-centre calibrator
+    against the oracle; T odd (a one-frame last step)."""
     from paper_1603_02126_gb300 import Plan
     rng = np.random.default_rng(500 + n)
     ant = synth.layout_disc(na, diam, rng, 0.5)
@@ -155,8 +157,8 @@ def test_fused_full_window_matches_oracle(n, na, diam):
     g_true = synth.true_gains(2, na, rng)
     T = 47
     E = synth.voltages(ant, freqs, g_true, sky, T, 1.0, rng).astype(np.complex64)
-    p = Plan(ant, freqs, n, 0.5, input="c64", path="fused")
-    assert p.info()["path"] == 1
+    p = Plan(ant, freqs, n, 0.5, input="c64", path=path)
+    assert p.info()["path"] == {"fused": 1, "unfused": 2}[path]
     cal = (sky[0, 0], sky[0, 1])
     g0 = synth.true_gains(2, na, rng)
     p.configure(cal, sky, 0.5, g0=g0)
