@@ -346,6 +346,19 @@ epic_status epical_fit_bandpass(epic_plan_t plan, int c_lo, int c_hi, int deg_am
  * Errors: INVALID_ARG (l0^2 + m0^2 >= 1), OOM, CUDA. */
 epic_status epic_set_phase_centre(epic_plan_t plan, double l0, double m0);
 
+/* Failure detection (no counterpart in the paper): the warp-specialised
+ * fused form (EPIC_PATH_PIPED) hands frames between its producer and
+ * consumer warps through mbarriers, and every wait gives up after a bounded
+ * number of polls; the kernel then raises the plan's error flag, stops
+ * waiting and runs to its end, and the next epic_plan_sync returns
+ * EPIC_ERR_TIMEOUT (the image of that call is not valid; the context stays
+ * usable).  This call sets that number of polls for the plan's later
+ * launches of that form (0 = the default, about 10^6); a small value makes
+ * the waits run out, which is how the timeout path is tested.  Kernels that
+ * have asynchronous copies in flight keep their own limits.  Host only.
+ * Errors: INVALID_ARG (polls < 0). */
+epic_status epic_plan_set_wait_limit(epic_plan_t plan, int polls);
+
 /* Wait for the plan's stream.  *n_held (may be NULL) receives the number
  * of held (antenna, channel) gains since the previous sync; the call
  * returns EPIC_ERR_NUMERIC if it is non-zero.  Synchronous. */

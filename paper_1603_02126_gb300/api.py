@@ -287,6 +287,10 @@ class Plan:
         """Phase the array to (l0, m0) (Sec. 2.1 footnote); resets EPICal."""
         B.check(self._lib.epic_set_phase_centre(self.handle, float(l0), float(m0)))
 
+    def set_wait_limit(self, polls):
+        """Polls per bounded wait of the warp-specialised kernel (0 = default)."""
+        B.check(self._lib.epic_plan_set_wait_limit(self.handle, int(polls)))
+
     def update(self, gains_out=None, status=None):
         torch = _torch()
         B.check(self._lib.epical_update(self.handle, _dptr(gains_out, torch.complex128, "gains_out"),

@@ -48,6 +48,7 @@ struct ImageArgs {
   size_t smem;             // dynamic shared memory bytes
   // multiple-pixel EPICal (0 pixels = off): the column-pass owner of each
   // calibration pixel stores E'(s_p, t) to ptap[t][C][npix] (tap order)
+  int wait_limit;           // warp-specialised form: polls per bounded wait (0 = default)
   int npix;
   const uint2* ptab;       // [COLROUNDS][BT] (slot mask, first tap index) per thread
   const float2* pph;       // [C][npix] window-coordinate phase of each pixel

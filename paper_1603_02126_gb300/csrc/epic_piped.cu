@@ -72,12 +72,12 @@ __device__ __forceinline__ bool mb_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; after a timeout (or once
-// any thread has timed out) it returns at once.
+// Bounded wait for the phase of the given parity (at most `limit` polls);
+// after a timeout (or once any thread has timed out) it returns at once.
 __device__ __forceinline__ void mb_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                        int* err) {
+                                        int* err, int limit) {
   if (*abort_flag) return;
-  for (int i = 0; i < kWaitLimit; ++i) {
+  for (int i = 0; i < limit; ++i) {
     if (mb_try(bar, parity)) return;
     if ((i & 255) == 255 && *abort_flag) return;
   }
@@ -154,7 +154,8 @@ __device__ __forceinline__ long long producer_unit(const ImageArgs& A, const Pip
     const int b = static_cast<int>(f & 1);
     const uint32_t ph = static_cast<uint32_t>((f >> 1) & 1);
     // slot b is free once the consumers have finished frame f - 2
-    if (f >= 2) mb_wait(smem_addr(S.bars + 2 + b), ph ^ 1u, S.abort_flag, A.err);
+    if (f >= 2) mb_wait(smem_addr(S.bars + 2 + b), ph ^ 1u, S.abort_flag, A.err,
+                        A.wait_limit > 0 ? A.wait_limit : kWaitLimit);
 
     float2* Es = S.Es + b * Na;
     float2* Er = S.Er + b * Na;
@@ -263,7 +264,7 @@ __device__ __forceinline__ long long consumer_unit(const ImageArgs& A, const Pip
   for (long long t = t0; t < t1; ++t, ++f) {
     const int b = static_cast<int>(f & 1);
     const uint32_t ph = static_cast<uint32_t>((f >> 1) & 1);
-    mb_wait(smem_addr(S.bars + b), ph, S.abort_flag, A.err);
+    mb_wait(smem_addr(S.bars + b), ph, S.abort_flag, A.err, A.wait_limit > 0 ? A.wait_limit : kWaitLimit);
     const float2* Tt = S.Tt + static_cast<size_t>(b) * N * rs;
 
     if (A.do_cal) {

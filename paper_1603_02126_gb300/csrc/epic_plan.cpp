@@ -159,6 +159,7 @@ struct epic_plan_s {
   int tune_cols = 4;            // unfused: column units per SM to aim for
   int tune_row_table = -1;      // unfused row kernel: gather table -1 auto, 0 L1, 1 shared memory
   int tune_row_frames = 2;      // unfused row kernel: frames per step
+  int wait_limit = 0;           // warp-specialised form: polls per bounded wait (0 = default)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
 
@@ -421,6 +422,7 @@ epic::ImageArgs fused_args(epic_plan_t p, const void* d_volt, long long n_time, 
   a.grid = static_cast<int>(std::min<long long>(units, p->ctas));
   a.smem = p->smem;
   a.npix = 0;                              // epic_image arms the pixel taps itself
+  a.wait_limit = p->wait_limit;
   return a;
 }
 
@@ -1587,6 +1589,13 @@ epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
   EPIC_CUDA(epic::launch_update(u, p->stream));
   p->frames = 0;
   p->iteration += 1;
+  return EPIC_OK;
+}
+
+epic_status epic_plan_set_wait_limit(epic_plan_t p, int polls) {
+  if (epic_status s = check_plan(p)) return s;
+  if (polls < 0) return fail(EPIC_ERR_INVALID_ARG, "polls must be >= 0");
+  p->wait_limit = polls;
   return EPIC_OK;
 }
 

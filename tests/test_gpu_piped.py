@@ -139,3 +139,29 @@ def test_piped_graph_replay_matches_direct_calls():
         res.append((img.cpu().numpy(), gout.cpu().numpy()))
     assert _rel(res[1][0], res[0][0]) <= 1e-6
     assert np.max(np.abs(res[1][1] - res[0][1]) / np.abs(res[0][1])) <= 1e-5
+
+
+def test_piped_bounded_wait_timeout_is_reported_and_recoverable():
+    """Failure detection without a fault: with one poll per bounded wait the
+    consumer warps give up waiting for the producers' first frame, the kernel
+    raises the plan's error flag, stops waiting and runs to its end, and
+    epic_plan_sync reports EPIC_ERR_TIMEOUT.  The context stays usable: with
+    the default limit restored the same plan images correctly again."""
+    from paper_1603_02126_gb300 import EpicError, Plan
+    w = synth.workload("lwa", n_time=64, n_chan=2)
+    rng = np.random.default_rng(12)
+    E = synth.voltages(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:40], 64, w["noise_power"], rng)
+    b = torch.from_numpy(synth.quantise_ci4(E, w["lsb"])).cuda()
+    kw = dict(support=3, param=0.5, input="ci4", voltage_scale=w["lsb"])
+    p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, path="piped", **kw)
+    assert p.info()["path"] == PIPED
+    p.set_wait_limit(1)
+    p.image(b)
+    with pytest.raises(EpicError) as ei:
+        p.sync()
+    assert ei.value.status == 6                       # EPIC_ERR_TIMEOUT
+    p.set_wait_limit(0)
+    img = p.image(b).cpu().numpy()
+    assert p.sync() == 0
+    ref = Plan(w["ant_xy"], w["freqs"], 128, 0.5, path="fused", **kw).image(b).cpu().numpy()
+    assert _rel(img, ref) <= IMG_TOL
