@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused image launch
 # on this workload, with kernel_sha() of the sources it was taken at;
 # ignored when those sources have changed since.
-TRAFFIC = {"kernel_sha": "f47c2e807e01", "bytes_per_launch": 182636288}
+TRAFFIC = {"kernel_sha": "992cfe64f2ec", "bytes_per_launch": 183077376}
 
 
 def kernel_sha() -> str:
@@ -275,7 +275,8 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
     g3 = torch.empty((C3, 2048), dtype=torch.complex128, device=dev)
     kw3 = dict(support=3, param=0.5, input="c64", stream=sc)
     frames3 = C3 * w3["n_time"]
-    p3 = Plan(w3["ant_xy"], w3["freqs"], 512, 0.5, path="unfused", workspace_bytes=2 << 30, **kw3)
+    # plain and batched forms with the same 8 GiB batch scratch
+    p3 = Plan(w3["ant_xy"], w3["freqs"], 512, 0.5, path="unfused", workspace_bytes=8 << 30, **kw3)
     p3.configure((0.0, 0.0), w3["model"], w3["gamma"])
     p3.image(v3, img3)
     p3.update(g3)
@@ -485,12 +486,34 @@ def profile_case(name):
         p.update()
         p.image(d, img)
         p.update()
+    elif name == "multipix_lwa":       # headline interval with 16 calibration pixels (Sec. 6)
+        w = synth.workload("lwa", n_time=2000)
+        d = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
+                                     w["noise_power"], w["lsb"], seed=1)
+        p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
+                 voltage_scale=w["lsb"], path="fused")
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        p.configure_pixels(w["model"][:16, :2])
+        img = p.image(d)
+        p.update()
+        p.image(d, img)
+        p.update()
+    elif name == "noise_lwa":          # Sec. 4 comparison path: X-engine and StEFCal, 64 channels
+        w = synth.workload("noise")
+        lsb = np.full(len(w["freqs"]), np.sqrt((w["sky"][:, 2].sum() + 10.0) / 2) / 2.0)
+        v = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], 4096, 10.0, lsb, seed=7)
+        p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, input="ci4", voltage_scale=lsb)
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+        for _ in range(2):
+            vis = p.visibilities(v)
+            g = torch.ones((len(w["freqs"]), w["ant_xy"].shape[0]), dtype=torch.complex128, device="cuda")
+            p.visibility_solve(vis, g, max_iter=2000, tol=1e-10)
     elif name == "hex_unfused":        # Na=2048 hex, N=512, 128 samples, plain unfused path
         w = synth.workload("hex2048", n_time=128)
         v = synth.voltages_c64_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"], w["n_time"],
                                      w["noise_power"], seed=3)
         p = Plan(w["ant_xy"], w["freqs"], 512, 0.5, support=3, param=0.5, input="c64",
-                 path="unfused", workspace_bytes=8 << 30)
+                 path="unfused", workspace_bytes=2 << 30)
         p.configure((0.0, 0.0), w["model"], w["gamma"])
         img = p.image(v)
         p.update()
@@ -551,7 +574,7 @@ def main():
                     help="skip the precision / batching / differentiation forms")
     ap.add_argument("--case", default=None,
                     help="run one untimed profiling workload (fused_lwa, tc_compact, unfused_lwa, "
-                         "grad_lwa, hex_unfused, cluster_compact) and exit")
+                         "grad_lwa, hex_unfused, cluster_compact, multipix_lwa, noise_lwa) and exit")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()

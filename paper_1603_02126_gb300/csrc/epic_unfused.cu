@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
 #pragma unroll
         for (int h = 0; h < H; ++h)
 #pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) dst[static_cast<size_t>(n1 + N1 * h + N2 * k1) * rsc] = v[h * N1 + k1];
+          for (int k1 = 0; k1 < N1; ++k1)        // streaming stores: keep L2 for the tap lists
+            __stcs(dst + static_cast<size_t>(n1 + N1 * h + N2 * k1) * rsc, v[h * N1 + k1]);
       }
     }
     it += nf;
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(c
 #pragma unroll
         for (int j = 0; j < N2; ++j) {
           const int jw = n1 + N1 * j;
-          v[j] = (j < NZ && jw < R) ? col[jw] : make_float2(0.f, 0.f);
+          v[j] = (j < NZ && jw < R) ? (STAGE ? col[jw] : __ldcs(col + jw)) : make_float2(0.f, 0.f);
         }
         fft::fft_lanes_p<N1, N2, NZ>(v, n1, z, tw, gmask);
 #pragma unroll
