@@ -276,9 +276,14 @@ epic_status epical_get_direction_gains(epic_plan_t plan, double* h_gains);
  * autocorrelations included.  d_volt: device [n_time][C][Na] as for
  * epic_image.  d_vis: device [C][Na][Na] complex128, caller-owned
  * (Hermitian: both triangles written); accumulate = 0 overwrites, else adds.
- * For 4-bit input the per-channel sums are exact integers (FP32 holds them
- * exactly below 2^24; segments of 32768 samples are added in FP64).
- * Asynchronous.  Errors: INVALID_ARG, CUDA. */
+ * For 4-bit input the product runs on the tensor cores: the samples are
+ * packed as FP16 integers into a plan-owned operand matrix (time segments
+ * that keep it within 1 GiB, grown on demand) and multiplied by tcgen05 MMAs
+ * with FP32 accumulation, every partial sum an integer below 2^24, so the
+ * per-channel sums are exact.  Complex64 input runs on the CUDA cores in
+ * FP32 (segments of 32768 samples added in FP64).
+ * Asynchronous.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT (bounded waits of
+ * the tensor-core kernel, through epic_plan_sync). */
 epic_status epic_visibilities(epic_plan_t plan, const void* d_volt, long long n_time, double* d_vis,
                               int accumulate);
 

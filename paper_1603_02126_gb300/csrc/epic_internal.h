@@ -115,6 +115,22 @@ struct XengineArgs {
   double2* vis;            // [C][Na][Na], accumulated (atomics)
 };
 cudaError_t launch_xengine(const XengineArgs& a, cudaStream_t s);
+// Tensor-core X-engine for 4-bit input (epic_tc.cu): pack to FP16 Z
+// [C][2 Na_p][Tp], then G = Z Z^T on tcgen05, upper-triangle tiles.
+struct XeTcArgs {
+  int n_chan, n_ant;
+  int na_p;                // antennas padded to a multiple of 64
+  int tp;                  // samples of this segment padded to a multiple of 64
+  const float* vscale;     // [C] or nullptr
+  double scale;            // 1 / T of the whole call
+  double2* vis;            // [C][Na][Na]
+  int accumulate;          // 1: add to vis, 0: overwrite
+  int* err;                // bounded-wait timeout flag
+};
+cudaError_t xe_prepare();
+bool xe_make_map(void* z, int n_chan, int na_p, int tp, void* tm);
+cudaError_t launch_xengine_tc(const XeTcArgs& a, const void* volt, long long t0, int nt, void* z, const void* tm,
+                              int sms, cudaStream_t s);
 cudaError_t launch_model_vis(int n_chan, int n_ant, int n_src, const double2* ph, const double* flux,
                              float2* vm, cudaStream_t s);
 struct StefcalArgs {

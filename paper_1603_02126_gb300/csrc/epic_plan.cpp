@@ -199,6 +199,10 @@ struct epic_plan_s {
   DevBuf<double2> d_uv;         // [C][Na] positions in wavelengths
   DevBuf<int> d_iters;          // [C] solver iterations
   bool vm_stale = true;
+  // tensor-core X-engine (4-bit input): FP16 operand scratch and its tensor map
+  DevBuf<uint16_t> d_xe_z;      // [C][2 Na_p][xe_tp]
+  int xe_tp = 0;                // samples per segment (multiple of 64); 0 = not set up
+  alignas(64) unsigned char tm_xe[128];
 
   // phase centre (Sec. 2.1 footnote): E_a multiplied by p_a = e^{+2 pi i u_a . s0}
   double phase_l = 0.0, phase_m = 0.0;
@@ -1099,6 +1103,7 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_ptap.release();
   p->d_vm.release();
   p->d_vis32.release();
+  p->d_xe_z.release();
   p->d_phase.release();
   p->d_bx.release();
   p->d_uv.release();
@@ -1293,6 +1298,41 @@ epic_status epic_visibilities(epic_plan_t p, const void* d_volt, long long n_tim
   if (!d_volt || !d_vis) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
   const size_t nv = static_cast<size_t>(p->nc) * p->na * p->na;
+  if (p->input == EPIC_IN_CI4) {
+    // tensor cores: FP16 integers, exact; time in segments that keep the
+    // operand scratch within 1 GiB (and every FP32 sum below 2^24)
+    const int na_p = (p->na + 63) / 64 * 64;
+    const size_t row_bytes = static_cast<size_t>(p->nc) * 2 * na_p * sizeof(uint16_t);
+    long long seg = static_cast<long long>((static_cast<size_t>(1) << 30) / row_bytes) / 64 * 64;
+    seg = std::max<long long>(64, std::min<long long>(seg, 32768));
+    seg = std::min<long long>(seg, (n_time + 63) / 64 * 64);
+    if (p->xe_tp < seg) {
+      EPIC_CUDA(cudaStreamSynchronize(p->stream));
+      if (p->xe_tp == 0) EPIC_CUDA(epic::xe_prepare());
+      if (p->d_xe_z.alloc(row_bytes / sizeof(uint16_t) * static_cast<size_t>(seg)) != cudaSuccess) {
+        p->xe_tp = 0;
+        return fail(EPIC_ERR_OOM, "X-engine operand scratch allocation failed");
+      }
+      if (!epic::xe_make_map(p->d_xe_z.p, p->nc, na_p, static_cast<int>(seg), p->tm_xe))
+        return fail(EPIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (X-engine)");
+      p->xe_tp = static_cast<int>(seg);
+    }
+    epic::XeTcArgs x{};
+    x.n_chan = p->nc;
+    x.n_ant = p->na;
+    x.na_p = na_p;
+    x.tp = p->xe_tp;
+    x.vscale = p->d_vscale.p;
+    x.scale = 1.0 / static_cast<double>(n_time);
+    x.vis = reinterpret_cast<double2*>(d_vis);
+    x.err = p->d_err.p;
+    for (long long t0 = 0; t0 < n_time; t0 += p->xe_tp) {
+      const int nt = static_cast<int>(std::min<long long>(p->xe_tp, n_time - t0));
+      x.accumulate = (t0 > 0 || accumulate) ? 1 : 0;
+      EPIC_CUDA(epic::launch_xengine_tc(x, d_volt, t0, nt, p->d_xe_z.p, p->tm_xe, p->sms, p->stream));
+    }
+    return EPIC_OK;
+  }
   if (!accumulate) EPIC_CUDA(cudaMemsetAsync(d_vis, 0, nv * sizeof(double2), p->stream));
   epic::XengineArgs a{};
   a.volt = d_volt;

@@ -460,6 +460,228 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// X-engine on the tensor cores (visibility comparison path, 4-bit input).
+// Per channel the voltages become a real matrix Z [2 Na_p][Tp] of FP16
+// integers (row 2a = Re E_a, row 2a + 1 = Im E_a, time contiguous, zero
+// padded); G = Z Z^T by tcgen05.mma (M = N = 128, K = 16 per instruction,
+// FP32 accumulation in TMEM), upper-triangle 128 x 128 tiles only.  The
+// 4-bit values and every partial sum are integers below 2^24, so G is
+// exact.  Epilogue: Re V_ab = G[2a][2b] + G[2a+1][2b+1],
+// Im V_ab = G[2a+1][2b] - G[2a][2b+1] (rows 2a and 2a+1 are adjacent TMEM
+// lanes, exchanged by one shuffle), times s_c^2 / T in FP64.
+// ---------------------------------------------------------------------------
+constexpr int kXeStages = 4;                 // K-chunk ring (A and B chunk per stage)
+constexpr int kXeThreads = 192;              // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t kXeStageBytes = 2 * kChunkBytes;
+
+size_t xe_smem_bytes() { return 1024 + kXeStages * kXeStageBytes + 256; }
+
+// volt [T][C][Na] 4-bit -> Z [C][2 Na_p][Tp] FP16; block = (channel, 32
+// antennas, 64 samples); thread = (row r of the 64, 16 samples).
+__global__ void __launch_bounds__(256) xe_pack_kernel(const unsigned char* __restrict__ volt, long long t0,
+                                                      int nt, int n_chan, int n_ant, int na_p, int tp,
+                                                      __half* __restrict__ z) {
+  __shared__ unsigned char tile[64][33];
+  const int c = blockIdx.x, ab = blockIdx.y * 32, tb = blockIdx.z * 64;
+  for (int i = threadIdx.x; i < 64 * 32; i += 256) {
+    const int tt = i / 32, k = i % 32;
+    const int t = tb + tt, a = ab + k;
+    tile[tt][k] = (t < nt && a < n_ant)
+                      ? __ldg(volt + (static_cast<size_t>(t0 + t) * n_chan + c) * n_ant + a)
+                      : static_cast<unsigned char>(0);
+  }
+  __syncthreads();
+  const int r = threadIdx.x / 4, q = threadIdx.x % 4;     // row 2k + s of the block, 16-sample quarter
+  const int k = r >> 1, sgn = r & 1;
+  __align__(16) __half v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const unsigned b = tile[q * 16 + j][k];
+    const int x = sgn ? static_cast<int>(b << 28) >> 28 : static_cast<int>(b << 24) >> 28;
+    v[j] = __int2half_rn(x);
+  }
+  __half* dst = z + (static_cast<size_t>(c) * 2 * na_p + 2 * ab + r) * tp + tb + q * 16;
+  reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(v)[0];
+  reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(v)[1];
+}
+
+__global__ void __launch_bounds__(kXeThreads, 1)
+    xengine_tc_kernel(const __grid_constant__ CUtensorMap tm_z, const XeTcArgs A) {
+  extern __shared__ __align__(1024) unsigned char xe_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(xe_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kXeStages * kXeStageBytes);
+  // bars: [0, S) full, [S, 2S) empty, 2S + {0, 1} tmem_full, 2S + {2, 3}
+  // tmem_empty, 2S + 4 drain (MMAs in flight after a timeout)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kXeStages + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kXeStages + 6);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = 2 * A.na_p / kTile;                        // row blocks per channel
+  const int pairs = nb * (nb + 1) / 2;
+  const long long tiles = static_cast<long long>(A.n_chan) * pairs;
+  const int kc_n = A.tp / 64;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kXeStages; ++i) {
+      mbar_init(smem_u32(bars + i), 1);
+      mbar_init(smem_u32(bars + kXeStages + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(bars + 2 * kXeStages + i), 1);
+      mbar_init(smem_u32(bars + 2 * kXeStages + 2 + i), 4);
+    }
+    mbar_init(smem_u32(bars + 2 * kXeStages + 4), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  // tile u -> (channel, row block bi, column block bj), bi <= bj
+  auto tile_of = [&](long long u, int* c, int* bi, int* bj) {
+    *c = static_cast<int>(u / pairs);
+    int pr = static_cast<int>(u - static_cast<long long>(*c) * pairs);
+    int i = 0;
+    while (pr >= nb - i) {
+      pr -= nb - i;
+      ++i;
+    }
+    *bi = i;
+    *bj = i + pr;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_z)) : "memory");
+      long long it = 0;                                       // K chunks issued so far
+      for (long long u = blockIdx.x; u < tiles && !*abort_flag; u += gridDim.x) {
+        int c, bi, bj;
+        tile_of(u, &c, &bi, &bj);
+        const int ya = c * 2 * A.na_p + bi * kTile, yb = c * 2 * A.na_p + bj * kTile;
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % kXeStages);
+          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
+          if (!mbar_wait(smem_u32(bars + kXeStages + s), ph ^ 1, abort_flag, A.err)) break;
+          const uint32_t bfull = smem_u32(bars + s);
+          mbar_expect_tx(bfull, kXeStageBytes);
+          unsigned char* st = base + s * kXeStageBytes;
+          tma_load_2d(smem_u32(st), &tm_z, kc * 64, ya, bfull);
+          tma_load_2d(smem_u32(st + kChunkBytes), &tm_z, kc * 64, yb, bfull);
+        }
+      }
+      if (*abort_flag) {
+        // let the last loads land before the CTA's shared memory is released
+        for (long long j = it > kXeStages ? it - kXeStages : 0; j < it; ++j) {
+          const uint32_t bar = smem_u32(bars + j % kXeStages), ph = static_cast<uint32_t>((j / kXeStages) & 1);
+          for (int w = 0; w < (1 << 22) && !mbar_try(bar, ph); ++w) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(kTile >> 3) << 17) |
+                             (static_cast<uint32_t>(kTile >> 4) << 24);   // FP16 x FP16 -> FP32
+      long long it = 0;
+      int i = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; ok && u < tiles; u += gridDim.x, ++i) {
+        const int acc = i & 1;
+        const uint32_t aph = (i >> 1) & 1;
+        if (!mbar_wait(smem_u32(bars + 2 * kXeStages + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % kXeStages);
+          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
+          if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(base + s * kXeStageBytes), b0 = a0 + kChunkBytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(d_tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc, (kc | k) != 0);
+          mma_commit(smem_u32(bars + kXeStages + s));          // stage free once these MMAs finish
+        }
+        if (ok) mma_commit(smem_u32(bars + 2 * kXeStages + acc));   // accumulator ready
+      }
+      if (*abort_flag) {
+        // MMAs still in flight must finish before TMEM is released
+        const uint32_t drain = smem_u32(bars + 2 * kXeStages + 4);
+        mma_commit(drain);
+        for (int w = 0; w < (1 << 22) && !mbar_try(drain, 0); ++w) {
+        }
+      }
+    }
+  } else {
+    // epilogue: warp (2..5) & 3 is the TMEM lane quarter it may read
+    const int q = warp & 3;
+    const int r = q * 32 + lane;                             // tile row 2a' + s
+    int i = 0;
+    for (long long u = blockIdx.x; u < tiles; u += gridDim.x, ++i) {
+      const int acc = i & 1;
+      const uint32_t aph = (i >> 1) & 1;
+      if (!mbar_wait(smem_u32(bars + 2 * kXeStages + acc), aph, abort_flag, A.err)) break;
+      tc_fence_after();
+      int c, bi, bj;
+      tile_of(u, &c, &bi, &bj);
+      const int a = (bi * kTile + r) >> 1;                   // antenna of this lane pair
+      const bool even = (lane & 1) == 0;
+      const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
+      const double sc = static_cast<double>(vs) * static_cast<double>(vs) * A.scale;
+      double2* V = A.vis + static_cast<size_t>(c) * A.n_ant * A.n_ant;
+#pragma unroll
+      for (int ch = 0; ch < kTile / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32), v);
+        // v[2j + s'] = G[r][bj*128 + ch*32 + 2j + s']; partner lane holds row r ^ 1
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float p0 = __shfl_xor_sync(fft::kFull, v[2 * j], 1);
+          const float p1 = __shfl_xor_sync(fft::kFull, v[2 * j + 1], 1);
+          if (even) {
+            const int b = (bj * kTile + ch * 32 + 2 * j) >> 1;
+            if (a < A.n_ant && b < A.n_ant) {
+              // row 2a: v = G[2a][2b], G[2a][2b+1]; partner: G[2a+1][2b], G[2a+1][2b+1]
+              const double re = (static_cast<double>(v[2 * j]) + static_cast<double>(p1)) * sc;
+              const double im = (static_cast<double>(p0) - static_cast<double>(v[2 * j + 1])) * sc;
+              double2* o = V + static_cast<size_t>(a) * A.n_ant + b;
+              if (A.accumulate) *o = make_double2(o->x + re, o->y + im);
+              else *o = make_double2(re, im);
+              if (bi != bj) {
+                double2* m = V + static_cast<size_t>(b) * A.n_ant + a;
+                if (A.accumulate) *m = make_double2(m->x + re, m->y - im);
+                else *m = make_double2(re, -im);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(bars + 2 * kXeStages + 2 + acc));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
 template <int N, typename T>
 cudaError_t rows_lp_n(const TcArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
   const size_t es_bytes = static_cast<size_t>(a.u.n_ant) * sizeof(float2);
@@ -515,6 +737,45 @@ cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_
   if (e != cudaSuccess) return e;
   if (a.u.do_cal) e = launch_correlate(a.u, t0, nt, s);
   return e;
+}
+
+cudaError_t xe_prepare() {
+  return cudaFuncSetAttribute(xengine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(xe_smem_bytes()));
+}
+
+bool xe_make_map(void* z, int n_chan, int na_p, int tp, void* tm) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(tp), static_cast<cuuint64_t>(n_chan) * 2 * na_p};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(tp) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kTile)};
+  cuuint32_t es[2] = {1, 1};
+  return encode(static_cast<CUtensorMap*>(tm), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, z, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_xengine_tc(const XeTcArgs& a, const void* volt, long long t0, int nt, void* z, const void* tm,
+                              int sms, cudaStream_t s) {
+  dim3 pg(static_cast<unsigned>(a.n_chan), static_cast<unsigned>(a.na_p / 32), static_cast<unsigned>(a.tp / 64));
+  xe_pack_kernel<<<pg, 256, 0, s>>>(static_cast<const unsigned char*>(volt), t0, nt, a.n_chan, a.n_ant, a.na_p,
+                                    a.tp, static_cast<__half*>(z));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nb = 2 * a.na_p / kTile;
+  const long long tiles = static_cast<long long>(a.n_chan) * nb * (nb + 1) / 2;
+  const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+  xengine_tc_kernel<<<grid, kXeThreads, xe_smem_bytes(), s>>>(*static_cast<const CUtensorMap*>(tm), a);
+  return cudaGetLastError();
 }
 
 // Tensor maps over the DFT matrix [2N][kp] and the spectra [C*N][tb_cap][kp].
