@@ -305,13 +305,21 @@ cudaError_t launch_cluster(int n, const ClusterArgs& a, cudaStream_t s);
 
 // Reduced-precision (tensor-core column DFT) batch, epic_tc.cu.
 struct TcArgs {
-  UnfusedArgs u;           // gridding inputs, grid scratch, image, pixel, EPICal sums
+  UnfusedArgs u;           // gridding inputs (window-column lists), image, pixel, EPICal sums
   void* hh;                // [C*N][tb_cap][kp] FP16/BF16 scaled row spectra
   float* fscale;           // [tb_cap*C] per-frame power-of-two scale s_f
   float* finv2;            // [tb_cap*C] 1 / s_f^2
   int tb_cap, kp, bf16;
   int* err;                // device flag: a bounded wait timed out
+  void* gh;                // [tb_cap*C*r_alloc][kr] FP16/BF16 scaled window grid
+  int kr;                  // K extent of the row DFT (2 x window columns, padded to 64)
+  int r_alloc;             // grid rows per frame in gh (max occupied rows)
+  const int4* win4;        // [C] (y0, rows, x0, cols)
+  const void* tm_gh;       // host CUtensorMap over gh
+  const void* tm_fr;       // host CUtensorMap over the row DFT matrix [2N][kr]
 };
+bool tc_make_row_maps(void* gh, void* dftr, long long rows_cap, int n, int kr, bool bf16, void* tm_gh,
+                      void* tm_fr);
 bool tc_supported(int n, int rows_alloc);
 int tc_kp(int rows_alloc);
 size_t tc_smem(int kp);

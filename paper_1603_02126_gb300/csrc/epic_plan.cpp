@@ -174,6 +174,11 @@ struct epic_plan_s {
   DevBuf<int> d_err;            // bounded-wait timeout flag
   alignas(64) unsigned char tm_dft[128];
   alignas(64) unsigned char tm_data[128];
+  int kr = 0;                   // K extent of the row DFT (2 x window columns, padded to 64)
+  DevBuf<uint16_t> d_tc_gh;     // [tc_time*C*rows_alloc][kr] scaled window grid
+  DevBuf<uint16_t> d_tc_dftr;   // [2N][kr] row DFT over window columns
+  alignas(64) unsigned char tm_gh[128];
+  alignas(64) unsigned char tm_fr[128];
 
   // cluster path (N = 256 / 512)
   int cs = 0, rpc_alloc = 0, clusters = 0, cl_step = 1;
@@ -569,15 +574,20 @@ uint16_t to_bf16_bits(float f) {
 epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double* d_image) {
   const int C = p->nc, N = p->n;
   if (p->tc_time == 0) {
+    p->kr = ((2 * *std::max_element(p->cols.begin(), p->cols.end()) + 63) / 64) * 64;
     const size_t per_t = static_cast<size_t>(C) *
-                         (static_cast<size_t>(N) * p->kp * 2 + 2 * sizeof(float) + sizeof(float2));
+                         (static_cast<size_t>(N) * p->kp * 2 + static_cast<size_t>(p->rows_alloc) * p->kr * 2 +
+                          2 * sizeof(float) + sizeof(float2));
     long long nt = static_cast<long long>(p->workspace_budget / per_t);
     nt = std::max<long long>(1, std::min<long long>(nt, 128));
     const size_t n_hh = static_cast<size_t>(C) * N * nt * p->kp;
+    const size_t n_gh = static_cast<size_t>(nt) * C * p->rows_alloc * p->kr;
     cudaError_t es[] = {p->d_tc_hh.alloc(n_hh),
                         p->d_tc_dft.alloc(static_cast<size_t>(2) * N * p->kp),
                         p->d_tc_scale.alloc(static_cast<size_t>(2 * nt) * C),
-                        p->d_tc_pix.alloc(static_cast<size_t>(nt) * C)};
+                        p->d_tc_pix.alloc(static_cast<size_t>(nt) * C),
+                        p->d_tc_gh.alloc(n_gh),
+                        p->d_tc_dftr.alloc(static_cast<size_t>(2) * N * p->kr)};
     for (cudaError_t x : es)
       if (x != cudaSuccess) return fail(EPIC_ERR_OOM, "tensor-path scratch allocation failed");
     EPIC_CUDA(cudaMemset(p->d_tc_hh.p, 0, n_hh * 2));
@@ -598,8 +608,26 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
         put(2 * ky + 1, 2 * jw + 1, cs);
       }
     EPIC_CUDA(cudaMemcpy(p->d_tc_dft.p, dft.data(), dft.size() * 2, cudaMemcpyHostToDevice));
+    // row DFT over window columns x: rows 2 kx + (re, im), columns 2 x + (re, im)
+    std::vector<uint16_t> dftr(static_cast<size_t>(2) * N * p->kr);
+    for (int kx = 0; kx < N; ++kx)
+      for (int x = 0; x < p->kr / 2; ++x) {
+        const long long m = (static_cast<long long>(x) * kx) % N;
+        const double th = 2.0 * kPi * static_cast<double>(m) / N;
+        const float cs = static_cast<float>(std::cos(th)), sn = static_cast<float>(std::sin(th));
+        auto put = [&](int r, int k, float v) {
+          dftr[static_cast<size_t>(r) * p->kr + k] = bf ? to_bf16_bits(v) : to_half_bits(v);
+        };
+        put(2 * kx, 2 * x, cs);
+        put(2 * kx, 2 * x + 1, -sn);
+        put(2 * kx + 1, 2 * x, sn);
+        put(2 * kx + 1, 2 * x + 1, cs);
+      }
+    EPIC_CUDA(cudaMemcpy(p->d_tc_dftr.p, dftr.data(), dftr.size() * 2, cudaMemcpyHostToDevice));
     if (!epic::tc_make_maps(p->d_tc_dft.p, p->d_tc_hh.p, N, C, static_cast<int>(nt), p->kp, bf, p->tm_dft,
-                            p->tm_data))
+                            p->tm_data) ||
+        !epic::tc_make_row_maps(p->d_tc_gh.p, p->d_tc_dftr.p, static_cast<long long>(nt) * C * p->rows_alloc, N,
+                                p->kr, bf, p->tm_gh, p->tm_fr))
       return fail(EPIC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     p->tc_time = static_cast<int>(nt);
   }
@@ -618,10 +646,10 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   u.win = p->d_win.p;
   u.twid = p->d_twid.p;
   u.spec = nullptr;
-  u.gofs = p->d_ugofs.p;
-  u.gcnt = p->d_ugcnt.p;
-  u.gent = p->d_ugent.p;
-  u.gbase = p->d_ugbase.p;
+  u.gofs = p->d_gofs.p;                    // window-column gather tables
+  u.gcnt = p->d_gcnt.p;
+  u.gent = p->d_gent.p;
+  u.gbase = p->d_gbase.p;
   u.pix = p->d_tc_pix.p;
   u.rows_alloc = p->rows_alloc;
   u.rs = p->rs;
@@ -641,6 +669,12 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   a.kp = p->kp;
   a.bf16 = p->precision == EPIC_PREC_BF16 ? 1 : 0;
   a.err = p->d_err.p;
+  a.gh = p->d_tc_gh.p;
+  a.kr = p->kr;
+  a.r_alloc = p->rows_alloc;
+  a.win4 = p->d_win4.p;
+  a.tm_gh = p->tm_gh;
+  a.tm_fr = p->tm_fr;
   for (long long t0 = 0; t0 < n_time; t0 += p->tc_time) {
     const int n = static_cast<int>(std::min<long long>(p->tc_time, n_time - t0));
     EPIC_CUDA(epic::launch_tc_batch(a, p->tm_dft, p->tm_data, t0, n, p->sms, p->stream));
@@ -965,14 +999,13 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       const int bx = p->base[ob], by = p->base[ob + 1];
       cellf[static_cast<size_t>(c) * Na + a] = (by - h - p->y0[c]) * ws + (bx - h - p->x0[c]);
     }
-  // gridding gather tables (see build_gather): the fused kernel and the
-  // plain unfused FP32 path grid in window columns, the fused path's adjoint
-  // and the reduced-precision row kernel in absolute columns
+  // gridding gather tables (see build_gather): the fused kernel, the plain
+  // unfused path and the reduced-precision gridding use window columns, the
+  // fused path's adjoint absolute columns
   std::vector<int> gofs, gbase, ugofs, ugbase;
   std::vector<uint4> gcnt, ugcnt;
   std::vector<uint2> gent, ugent;
-  const bool unfused_fp32 = p->path == EPIC_PATH_UNFUSED && p->precision == EPIC_PREC_FP32;
-  if (p->path == EPIC_PATH_FUSED || unfused_fp32) {
+  if (p->path == EPIC_PATH_FUSED || p->path == EPIC_PATH_UNFUSED) {
     const int n1 = p->path == EPIC_PATH_FUSED ? epic::image_fft_lanes(N) : epic::unfused_fft_lanes(N);
     if (epic_status st = build_gather(p, wts, n1, true, gofs, gcnt, gent, gbase)) {
       epic_plan_destroy(p);
@@ -980,8 +1013,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
     for (int c = 0; c < C; ++c) p->gmax = std::max(p->gmax, gbase[c + 1] - gbase[c]);
   }
-  if (p->path == EPIC_PATH_FUSED || (p->path == EPIC_PATH_UNFUSED && !unfused_fp32)) {
-    const int n1 = p->path == EPIC_PATH_UNFUSED ? epic::unfused_fft_lanes(N) : epic::image_fft_lanes(N);
+  if (p->path == EPIC_PATH_FUSED) {
+    const int n1 = epic::image_fft_lanes(N);
     if (epic_status st = build_gather(p, wts, n1, false, ugofs, ugcnt, ugent, ugbase)) {
       epic_plan_destroy(p);
       return st;
@@ -1093,6 +1126,8 @@ epic_status epic_plan_destroy(epic_plan_t p) {
   p->d_tc_dft.release();
   p->d_tc_scale.release();
   p->d_tc_pix.release();
+  p->d_tc_gh.release();
+  p->d_tc_dftr.release();
   p->d_err.release();
   p->d_ap.release();
   p->d_dp.release();

@@ -1,36 +1,40 @@
-// Reduced-precision EPIC imaging: the column transform of Eq. 10 as a
-// tensor-core GEMM (tcgen05, FP16 or BF16 operands, FP32 accumulation).
+// Reduced-precision EPIC imaging: both 1-D transforms of Eq. 10 as
+// tensor-core GEMMs (tcgen05, FP16 or BF16 operands, FP32 accumulation).
 //
 // Per batch of frames (frame f = t_local * C + c):
 //   frame_scale  S_f = sum_a |w_a E_a| / Na, an upper bound of every row
 //                spectrum value; s_f = largest power of two with s_f S_f < 1;
-//   rows_lp      per frame, E' = E / g (Eq. 8) into shared memory, FP32
-//                gridding (Eq. 9) as a gather straight into the FFT lanes of
-//                every occupied grid row (the plain path's tap lists) and the
-//                FP32 N-point row FFT; the spectrum is
-//                scaled by s_f, rounded to FP16/BF16 and stored K-major as
-//                Hh[c][kx][t][2 jw + (re, im)]; the calibrator pixel is
-//                summed in FP32 from the same spectra;
+//   grid_lp      per frame, E' = E / g (Eq. 8) into shared memory, FP32
+//                gridding (Eq. 9) as a gather into the window grid (the
+//                plain path's window-column lists), scaled by s_f and stored
+//                FP16/BF16 as Gh[f R + jw][2 x + (re, im)]; the calibrator
+//                pixel is summed in FP32 from the same cells;
+//   tc_rows      H = Gh F_r^T with the real-expanded DFT over window columns
+//                (outputs 2 kx + (re, im)); the epilogue writes each row's
+//                spectrum K-major as Hh[c][kx][t][2 jw + (re, im)];
 //   tc_cols      D[r][t] = sum_k' F[r][k'] Hh[c][kx][t][k'] with the
 //                real-expanded DFT matrix F (rows r = 2 ky + (re, im),
 //                columns k' = 2 jw + (re, im)); TMEM lane r then sums
 //                D[r][t]^2 / s_t^2 over the frames t of the tile, lanes 2ky and
 //                2ky+1 are added and the result goes to image[c][ky][kx]
 //                (FP64 atomics).  |E|^2 does not depend on where the window
-//                starts, so F uses window rows jw.
+//                starts, so both DFTs use window coordinates.
 // tc_cols is a persistent, warp-specialised kernel: warp 0 issues TMA loads
 // (128B-swizzled, 2-stage ring of data tiles; the CTA's DFT tile is loaded
 // once), warp 1 owns the TMEM allocation and issues tcgen05.mma from one
 // thread (M = 128 DFT rows, N = 128 frames, K = 16 per instruction), warps
 // 2-9 drain the double-buffered TMEM accumulators (two warps per lane
-// quarter, 64 frames each).  Every mbarrier wait is
-// bounded; on timeout the kernel records an error flag and winds down.
+// quarter, 64 frames each).  tc_rows and the X-engine stream both operands
+// through a 4-stage ring (warps 0, 1, and 2-5 for the epilogue).  Every
+// mbarrier wait is bounded; on timeout the kernel records an error flag and
+// winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "epic_fft.cuh"
 #include "epic_internal.h"
@@ -100,99 +104,89 @@ __global__ void frame_scale_kernel(const TcArgs A, long long t0, int nt) {
   }
 }
 
-// ---- FP32 row FFTs, low-precision K-major output, FP32 calibrator pixel ----
+// ---- gridding into the low-precision window grid, FP32 calibrator pixel ----
+// One frame at a time per CTA: E' = E / g (Eq. 8) into shared memory, then
+// every lane (window row jw, n1) gathers the taps of its window columns
+// x = n1 + N1 j (Eq. 9, the plan's window-column lists), scales by s_f and
+// stores the cell rounded to FP16/BF16 into Gh[f R_alloc + jw][2x + re/im]
+// (columns without taps get zeros).  The calibrator pixel, the Eq. 10 sum
+// at k0, is accumulated from the FP32 cells with their absolute phases.
 template <int N, typename T>
-__global__ void __launch_bounds__(kLBT) rows_lp_kernel(const TcArgs A, long long t0, int nt) {
-  constexpr int N1 = LCfg<N>::N1, N2 = LCfg<N>::N2, H = N2 / N1;
-  constexpr int GROUPS = kLBT / N1, GPW = 32 / N1;
-  constexpr int CW = (N2 + 15) / 16;               // uint4 words of group lengths per lane
-  using X = fft::Xchg<N1, N2>;
-  __shared__ float2 tw[N];
-  __shared__ float2 zbuf[GROUPS * X::ZG];
+__global__ void __launch_bounds__(kLBT) grid_lp_kernel(const TcArgs A, long long t0, int nt) {
+  constexpr int N1 = LCfg<N>::N1, N2 = LCfg<N>::N2;
+  constexpr int GROUPS = kLBT / N1;
+  constexpr int CW = (N2 + 15) / 16;
   extern __shared__ float2 Es[];                   // [Na] E / g of the current frame
-  for (int i = threadIdx.x; i < N; i += kLBT) tw[i] = A.u.twid[i];
   const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
-  float2* z = zbuf + g * X::ZG;
+  const int lane = threadIdx.x & 31;
   const int C = A.u.n_chan, Na = A.u.n_ant;
-  const int pn1 = A.u.k0x % N1, pq = A.u.k0x / N1;
-  const int pslot = (pq % H) * N1 + pq / H;
-  T* hh = static_cast<T*>(A.hh);
+  const int nj = A.kr / (2 * N1);                  // column blocks held in Gh
+  T* gh = static_cast<T*>(A.gh);
   const long long frames = static_cast<long long>(nt) * C;
-  // item = c * nt + tl: a CTA's consecutive items stay in one channel
   for (long long it = blockIdx.x; it < frames; it += gridDim.x) {
     const int c = static_cast<int>(it / nt);
     const int tl = static_cast<int>(it - static_cast<long long>(c) * nt);
     const size_t f = static_cast<size_t>(tl) * C + c;
     const float vs = A.u.vscale ? __ldg(A.u.vscale + c) : 1.0f;
-    __syncthreads();                               // previous frame's gathers are done
+    __syncthreads();
     for (int a = threadIdx.x; a < Na; a += kLBT) {
       const float2 e = load_volt_tc(A.u.volt, A.u.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
       Es[a] = fft::cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a));
     }
     __syncthreads();
-    const int2 wn = __ldg(A.u.win + c);
+    const int4 wn = __ldg(A.win4 + c);             // (y0, rows, x0, cols)
     const int R = wn.y;
-    const int* gofs = A.u.gofs + static_cast<size_t>(c) * A.u.rows_alloc * N1;
-    const uint4* gcnt = A.u.gcnt + static_cast<size_t>(c) * A.u.rows_alloc * N1 * CW;
+    const int nl = A.u.rows_alloc * N1;
+    const int* gofs = A.u.gofs + static_cast<size_t>(c) * nl;
+    const uint4* gcnt = A.u.gcnt + static_cast<size_t>(c) * nl * CW;
     const uint2* gent = A.u.gent + __ldg(A.u.gbase + c);
     const float sf = __ldg(A.fscale + f);
-    for (int rb = g - g % GPW; rb < R; rb += GROUPS) {
-      const int row = rb + g % GPW;
-      const bool live = row < R;
-      float2 v[N2];
+    float2 pix = make_float2(0.f, 0.f);
+    for (int row = g; row < R; row += GROUPS) {
+      const int li = row * N1 + n1;
+      int e = __ldg(gofs + li);
+      unsigned cv[4 * CW];
 #pragma unroll
-      for (int j = 0; j < N2; ++j) v[j] = make_float2(0.f, 0.f);
-      if (live) {
-        // gridding (Eq. 9) as a gather into this lane's columns n1 + N1 j
-        const int li = row * N1 + n1;
-        int e = __ldg(gofs + li);
-        unsigned cv[4 * CW];
+      for (int w = 0; w < CW; ++w) {
+        const uint4 q = __ldg(gcnt + static_cast<size_t>(li) * CW + w);
+        cv[4 * w] = q.x;
+        cv[4 * w + 1] = q.y;
+        cv[4 * w + 2] = q.z;
+        cv[4 * w + 3] = q.w;
+      }
+      T* dst = gh + (f * A.r_alloc + row) * static_cast<size_t>(A.kr);
 #pragma unroll
-        for (int w = 0; w < CW; ++w) {
-          const uint4 q = __ldg(gcnt + static_cast<size_t>(li) * CW + w);
-          cv[4 * w] = q.x;
-          cv[4 * w + 1] = q.y;
-          cv[4 * w + 2] = q.z;
-          cv[4 * w + 3] = q.w;
+      for (int j = 0; j < N2; ++j) {
+        if (j >= nj) break;
+        const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
+        float2 sum = make_float2(0.f, 0.f);
+        for (int k = 0; k < cj; ++k) {
+          const uint2 en = __ldg(gent + e + k);
+          const float2 x = Es[en.x];
+          const float w = __uint_as_float(en.y);
+          sum.x = fmaf(w, x.x, sum.x);
+          sum.y = fmaf(w, x.y, sum.y);
         }
-#pragma unroll
-        for (int j = 0; j < N2; ++j) {
-          const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
-          float2 sum = make_float2(0.f, 0.f);
-          for (int k = 0; k < cj; ++k) {
-            const uint2 en = __ldg(gent + e + k);
-            const float2 x = Es[en.x];
-            const float w = __uint_as_float(en.y);
-            sum.x = fmaf(w, x.x, sum.x);
-            sum.y = fmaf(w, x.y, sum.y);
-          }
-          e += cj;
-          v[j] = sum;
+        e += cj;
+        const int x = n1 + N1 * j;
+        store_lp(dst + 2 * x, sum.x * sf, sum.y * sf);
+        if (A.u.do_cal && cj > 0) {
+          const int m = ((wn.z + x) * A.u.k0x + (wn.x + row) * A.u.k0y) & (N - 1);
+          const float2 t = __ldg(A.u.twid + m);
+          pix.x += sum.x * t.x - sum.y * t.y;
+          pix.y += sum.x * t.y + sum.y * t.x;
         }
       }
-      fft::fft_lanes<N1, N2>(v, n1, z, tw, fft::kFull);
-      if (live) {
+    }
+    if (A.u.do_cal) {
 #pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const int kx = n1 + N1 * h + N2 * k1;
-            const float2 x = v[h * N1 + k1];
-            T* dst = hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * row;
-            store_lp(dst, x.x * sf, x.y * sf);
-          }
-        if (A.u.do_cal && n1 == pn1) {
-          // pixel (k0x, k0y): sum over rows of X[jy][k0x] e^{+2 pi i jy k0y / N}
-          float2 x = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int q = 0; q < N2; ++q)
-            if (q == pslot) x = v[q];
-          const int jy = wn.x + row;
-          const float2 t = tw[(jy * A.u.k0y) & (N - 1)];
-          const float2 y = fft::cmul(x, t);
-          atomicAdd(&A.u.pix[f].x, y.x * A.u.pix_sign);
-          atomicAdd(&A.u.pix[f].y, y.y * A.u.pix_sign);
-        }
+      for (int o = 16; o > 0; o >>= 1) {
+        pix.x += __shfl_xor_sync(fft::kFull, pix.x, o);
+        pix.y += __shfl_xor_sync(fft::kFull, pix.y, o);
+      }
+      if (lane == 0 && (pix.x != 0.f || pix.y != 0.f)) {
+        atomicAdd(&A.u.pix[f].x, pix.x * A.u.pix_sign);
+        atomicAdd(&A.u.pix[f].y, pix.y * A.u.pix_sign);
       }
     }
   }
@@ -682,19 +676,173 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   }
 }
 
+// Row DFT of the precision form on the tensor cores: H = Gh F_r^T, rows =
+// (frame, window row), K = 2 x window columns (re/im interleaved), outputs
+// (kx, re/im) with F_r the real-expanded DFT over window columns.  Tile =
+// (128 rows, 128 outputs); warp 0 streams 64-element K chunks of both
+// operands through the mbarrier ring, warp 1 issues the MMAs, warps 2-5
+// write each lane's (re, im) pairs of its frame and window row straight into
+// the column GEMM's K-major operand Hh[c][kx][t][2 jw + re/im], skipping
+// rows past the channel's occupied rows (they stay zero).
+template <bool kBf16>
+__global__ void __launch_bounds__(kXeThreads, 1)
+    tc_rows_kernel(const __grid_constant__ CUtensorMap tm_gh, const __grid_constant__ CUtensorMap tm_fr,
+                   const TcArgs A, int nt) {
+  using T = typename std::conditional<kBf16, __nv_bfloat16, __half>::type;
+  extern __shared__ __align__(1024) unsigned char tr_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tr_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kXeStages * kXeStageBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kXeStages + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kXeStages + 6);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = A.u.n_chan, N = A.u.grid_n;
+  const long long rows = static_cast<long long>(nt) * C * A.r_alloc;
+  const long long mt_n = (rows + kTile - 1) / kTile;
+  const int nt2 = 2 * N / kTile;
+  const long long tiles = mt_n * nt2;
+  const int kc_n = A.kr / 64;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kXeStages; ++i) {
+      mbar_init(smem_u32(bars + i), 1);
+      mbar_init(smem_u32(bars + kXeStages + i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(bars + 2 * kXeStages + i), 1);
+      mbar_init(smem_u32(bars + 2 * kXeStages + 2 + i), 4);
+    }
+    mbar_init(smem_u32(bars + 2 * kXeStages + 4), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_gh)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_fr)) : "memory");
+      long long it = 0;
+      for (long long u = blockIdx.x; u < tiles && !*abort_flag; u += gridDim.x) {
+        const int mt = static_cast<int>(u / nt2), ot = static_cast<int>(u % nt2);
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % kXeStages);
+          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
+          if (!mbar_wait(smem_u32(bars + kXeStages + s), ph ^ 1, abort_flag, A.err)) break;
+          const uint32_t bfull = smem_u32(bars + s);
+          mbar_expect_tx(bfull, kXeStageBytes);
+          unsigned char* st = base + s * kXeStageBytes;
+          tma_load_2d(smem_u32(st), &tm_gh, kc * 64, mt * kTile, bfull);
+          tma_load_2d(smem_u32(st + kChunkBytes), &tm_fr, kc * 64, ot * kTile, bfull);
+        }
+      }
+      if (*abort_flag) {
+        for (long long j = it > kXeStages ? it - kXeStages : 0; j < it; ++j) {
+          const uint32_t bar = smem_u32(bars + j % kXeStages), ph = static_cast<uint32_t>((j / kXeStages) & 1);
+          for (int w = 0; w < (1 << 22) && !mbar_try(bar, ph); ++w) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((kBf16 ? 1u : 0u) << 7) | ((kBf16 ? 1u : 0u) << 10) |
+                             (static_cast<uint32_t>(kTile >> 3) << 17) | (static_cast<uint32_t>(kTile >> 4) << 24);
+      long long it = 0;
+      int i = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; ok && u < tiles; u += gridDim.x, ++i) {
+        const int acc = i & 1;
+        const uint32_t aph = (i >> 1) & 1;
+        if (!mbar_wait(smem_u32(bars + 2 * kXeStages + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % kXeStages);
+          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
+          if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(base + s * kXeStageBytes), b0 = a0 + kChunkBytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(d_tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc, (kc | k) != 0);
+          mma_commit(smem_u32(bars + kXeStages + s));
+        }
+        if (ok) mma_commit(smem_u32(bars + 2 * kXeStages + acc));
+      }
+      if (*abort_flag) {
+        const uint32_t drain = smem_u32(bars + 2 * kXeStages + 4);
+        mma_commit(drain);
+        for (int w = 0; w < (1 << 22) && !mbar_try(drain, 0); ++w) {
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    T* hh = static_cast<T*>(A.hh);
+    int i = 0;
+    for (long long u = blockIdx.x; u < tiles; u += gridDim.x, ++i) {
+      const int acc = i & 1;
+      const uint32_t aph = (i >> 1) & 1;
+      if (!mbar_wait(smem_u32(bars + 2 * kXeStages + acc), aph, abort_flag, A.err)) break;
+      tc_fence_after();
+      const int mt = static_cast<int>(u / nt2), ot = static_cast<int>(u % nt2);
+      const long long row = static_cast<long long>(mt) * kTile + q * 32 + lane;
+      const long long f = row / A.r_alloc;                 // frame tl * C + c
+      const int jw = static_cast<int>(row - f * A.r_alloc);
+      const int c = static_cast<int>(f % C), tl = static_cast<int>(f / C);
+      const bool live = row < rows && jw < __ldg(A.win4 + (row < rows ? c : 0)).y;
+#pragma unroll
+      for (int ch = 0; ch < kTile / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32), v);
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int kx = (ot * kTile + ch * 32) / 2 + j;
+            store_lp(hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * jw, v[2 * j], v[2 * j + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(bars + 2 * kXeStages + 2 + acc));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
 template <int N, typename T>
-cudaError_t rows_lp_n(const TcArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
+cudaError_t grid_lp_n(const TcArgs& a, long long t0, int nt, int sms, cudaStream_t s) {
   const size_t es_bytes = static_cast<size_t>(a.u.n_ant) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(rows_lp_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(grid_lp_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(es_bytes));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_lp_kernel<N, T>, kLBT, es_bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_lp_kernel<N, T>, kLBT, es_bytes);
   if (e != cudaSuccess) return e;
   const long long frames = static_cast<long long>(nt) * a.u.n_chan;
   long long rb = static_cast<long long>(per_sm > 0 ? per_sm : 1) * sms;
   if (rb > frames) rb = frames;
-  rows_lp_kernel<N, T><<<static_cast<unsigned>(rb), kLBT, es_bytes, s>>>(a, t0, nt);
+  grid_lp_kernel<N, T><<<static_cast<unsigned>(rb), kLBT, es_bytes, s>>>(a, t0, nt);
   return cudaGetLastError();
 }
 
@@ -707,11 +855,44 @@ int tc_kp(int rows_alloc) { return ((2 * rows_alloc + 63) / 64) * 64; }
 size_t tc_smem(int kp) { return tc_smem_bytes(kp); }
 
 cudaError_t tc_prepare(bool bf16, size_t smem) {
+  cudaError_t e = bf16 ? cudaFuncSetAttribute(tc_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(xe_smem_bytes()))
+                       : cudaFuncSetAttribute(tc_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(xe_smem_bytes()));
+  if (e != cudaSuccess) return e;
   if (bf16)
     return cudaFuncSetAttribute(tc_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem));
   return cudaFuncSetAttribute(tc_cols_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(smem));
+}
+
+// Tensor maps over the window grid Gh [rows_cap][kr] and the row DFT [2N][kr].
+bool tc_make_row_maps(void* gh, void* dftr, long long rows_cap, int n, int kr, bool bf16, void* tm_gh,
+                      void* tm_fr) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(kr) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kTile)};
+  cuuint32_t es[2] = {1, 1};
+  cuuint64_t dg[2] = {static_cast<cuuint64_t>(kr), static_cast<cuuint64_t>(rows_cap)};
+  if (encode(static_cast<CUtensorMap*>(tm_gh), dt, 2, gh, dg, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  cuuint64_t df[2] = {static_cast<cuuint64_t>(kr), static_cast<cuuint64_t>(2 * n)};
+  return encode(static_cast<CUtensorMap*>(tm_fr), dt, 2, dftr, df, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_data, long long t0, int nt,
@@ -721,11 +902,22 @@ cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_
   if (e != cudaSuccess) return e;
   const int frames = nt * a.u.n_chan;
   frame_scale_kernel<<<(frames * 32 + 255) / 256, 256, 0, s>>>(a, t0, nt);
-  if (a.bf16) e = (a.u.grid_n == 128) ? rows_lp_n<128, __nv_bfloat16>(a, t0, nt, sms, s)
-                                      : rows_lp_n<256, __nv_bfloat16>(a, t0, nt, sms, s);
-  else e = (a.u.grid_n == 128) ? rows_lp_n<128, __half>(a, t0, nt, sms, s)
-                               : rows_lp_n<256, __half>(a, t0, nt, sms, s);
+  if (a.bf16) e = (a.u.grid_n == 128) ? grid_lp_n<128, __nv_bfloat16>(a, t0, nt, sms, s)
+                                      : grid_lp_n<256, __nv_bfloat16>(a, t0, nt, sms, s);
+  else e = (a.u.grid_n == 128) ? grid_lp_n<128, __half>(a, t0, nt, sms, s)
+                               : grid_lp_n<256, __half>(a, t0, nt, sms, s);
   if (e != cudaSuccess) return e;
+  {
+    const long long rows = static_cast<long long>(nt) * a.u.n_chan * a.r_alloc;
+    const long long tiles = (rows + kTile - 1) / kTile * (2 * a.u.grid_n / kTile);
+    const int grid = static_cast<int>(tiles < sms ? tiles : sms);
+    const CUtensorMap* tg = static_cast<const CUtensorMap*>(a.tm_gh);
+    const CUtensorMap* tf = static_cast<const CUtensorMap*>(a.tm_fr);
+    if (a.bf16) tc_rows_kernel<true><<<grid, kXeThreads, xe_smem_bytes(), s>>>(*tg, *tf, a, nt);
+    else tc_rows_kernel<false><<<grid, kXeThreads, xe_smem_bytes(), s>>>(*tg, *tf, a, nt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int MB = 2 * a.u.grid_n / kTile;
   const int grid = (sms / MB) * MB;
   const size_t smem = tc_smem_bytes(a.kp);
