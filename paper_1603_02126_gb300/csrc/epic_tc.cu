@@ -2,9 +2,10 @@
 // tensor-core GEMMs (tcgen05, FP16 or BF16 operands, FP32 accumulation).
 //
 // Per batch of frames (frame f = t_local * C + c):
-//   frame_scale  S_f = sum_a |w_a E_a| / Na, an upper bound of every row
-//                spectrum value; s_f = largest power of two with s_f S_f < 1;
-//   grid_lp      per frame, E' = E / g (Eq. 8) into shared memory, FP32
+//   grid_lp      per frame, E' = E / g (Eq. 8) into shared memory and
+//                S_f = sum_a |E'_a| / Na, an upper bound of every grid cell
+//                and row-spectrum value (s_f = largest power of two with
+//                s_f S_f < 1); FP32
 //                gridding (Eq. 9) as a gather into the window grid (the
 //                plain path's window-column lists), scaled by s_f and stored
 //                FP16/BF16 as Gh[f R + jw][2 x + (re, im)]; the calibrator
@@ -79,31 +80,6 @@ __device__ __forceinline__ void store_lp(__nv_bfloat16* dst, float re, float im)
   *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(re, im);
 }
 
-// ---- S_f: one warp per frame ----
-__global__ void frame_scale_kernel(const TcArgs A, long long t0, int nt) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int C = A.u.n_chan, Na = A.u.n_ant;
-  if (warp >= nt * C) return;
-  const int c = warp % C, tl = warp / C;
-  const float vs = A.u.vscale ? __ldg(A.u.vscale + c) : 1.0f;
-  float s = 0.f;
-  for (int a = lane; a < Na; a += 32) {
-    if (__ldg(A.u.cell0 + static_cast<size_t>(c) * Na + a) < 0) continue;
-    const float2 e = load_volt_tc(A.u.volt, A.u.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
-    const float2 w = __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a);
-    const float2 ec = fft::cmul(make_float2(e.x * vs, e.y * vs), w);
-    s += sqrtf(ec.x * ec.x + ec.y * ec.y);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(fft::kFull, s, o);
-  if (lane == 0) {
-    const int k = pow2_exp_below_inverse(s / static_cast<float>(Na));
-    A.fscale[warp] = exp2i(k);        // s_f: multiplies the row spectra
-    A.finv2[warp] = exp2i(-2 * k);    // 1 / s_f^2: multiplies |D|^2
-  }
-}
-
 // ---- gridding into the low-precision window grid, FP32 calibrator pixel ----
 // One frame at a time per CTA: E' = E / g (Eq. 8) into shared memory, then
 // every lane (window row jw, n1) gathers the taps of its window columns
@@ -117,6 +93,7 @@ __global__ void __launch_bounds__(kLBT) grid_lp_kernel(const TcArgs A, long long
   constexpr int GROUPS = kLBT / N1;
   constexpr int CW = (N2 + 15) / 16;
   extern __shared__ float2 Es[];                   // [Na] E / g of the current frame
+  __shared__ float red[kLBT / 32];
   const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
   const int lane = threadIdx.x & 31;
   const int C = A.u.n_chan, Na = A.u.n_ant;
@@ -129,18 +106,34 @@ __global__ void __launch_bounds__(kLBT) grid_lp_kernel(const TcArgs A, long long
     const size_t f = static_cast<size_t>(tl) * C + c;
     const float vs = A.u.vscale ? __ldg(A.u.vscale + c) : 1.0f;
     __syncthreads();
+    // E' and S_f = sum_a |E'_a| / Na over unflagged antennas: an upper bound
+    // of every grid cell and row-spectrum value (normalised taps, 1/Na folded)
+    float sa = 0.f;
     for (int a = threadIdx.x; a < Na; a += kLBT) {
       const float2 e = load_volt_tc(A.u.volt, A.u.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
-      Es[a] = fft::cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a));
+      const float2 ec = fft::cmul(make_float2(e.x * vs, e.y * vs), __ldg(A.u.wgain + static_cast<size_t>(c) * Na + a));
+      Es[a] = ec;
+      if (__ldg(A.u.cell0 + static_cast<size_t>(c) * Na + a) >= 0) sa += sqrtf(ec.x * ec.x + ec.y * ec.y);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(fft::kFull, sa, o);
+    if (lane == 0) red[threadIdx.x >> 5] = sa;
     __syncthreads();
+    float S = 0.f;
+#pragma unroll
+    for (int w = 0; w < kLBT / 32; ++w) S += red[w];
+    const int ke = pow2_exp_below_inverse(S / static_cast<float>(Na));
+    const float sf = exp2i(ke);                    // s_f multiplies the cells
+    if (threadIdx.x == 0) {
+      A.fscale[f] = sf;
+      A.finv2[f] = exp2i(-2 * ke);                 // 1 / s_f^2 multiplies |D|^2
+    }
     const int4 wn = __ldg(A.win4 + c);             // (y0, rows, x0, cols)
     const int R = wn.y;
     const int nl = A.u.rows_alloc * N1;
     const int* gofs = A.u.gofs + static_cast<size_t>(c) * nl;
     const uint4* gcnt = A.u.gcnt + static_cast<size_t>(c) * nl * CW;
     const uint2* gent = A.u.gent + __ldg(A.u.gbase + c);
-    const float sf = __ldg(A.fscale + f);
     float2 pix = make_float2(0.f, 0.f);
     for (int row = g; row < R; row += GROUPS) {
       const int li = row * N1 + n1;
@@ -900,8 +893,6 @@ cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_
   cudaError_t e = cudaSuccess;
   if (a.u.do_cal) e = cudaMemsetAsync(a.u.pix, 0, static_cast<size_t>(nt) * a.u.n_chan * sizeof(float2), s);
   if (e != cudaSuccess) return e;
-  const int frames = nt * a.u.n_chan;
-  frame_scale_kernel<<<(frames * 32 + 255) / 256, 256, 0, s>>>(a, t0, nt);
   if (a.bf16) e = (a.u.grid_n == 128) ? grid_lp_n<128, __nv_bfloat16>(a, t0, nt, sms, s)
                                       : grid_lp_n<256, __nv_bfloat16>(a, t0, nt, sms, s);
   else e = (a.u.grid_n == 128) ? grid_lp_n<128, __half>(a, t0, nt, sms, s)
