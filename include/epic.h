@@ -89,6 +89,10 @@ typedef struct {
   size_t workspace_bytes;      /* UNFUSED batch scratch budget; 0 = 2 GiB */
   const double* kernel_param_ant;  /* host [Na]: kernel_param per antenna (heterogeneous
                                       illumination patterns), or NULL = kernel_param for all */
+  int batch_persistent;        /* UNFUSED FP32, N = 256 or 512: 1 = every epic_image call is one
+                                  persistent cooperative launch over all its batches (grid
+                                  barriers between the row, column and correlation phases);
+                                  0 = one launch per kernel and batch; epic_autotune may switch it */
 } epic_plan_desc;
 
 /* Read-only facts about a plan (epic_plan_get_info). */
@@ -115,6 +119,7 @@ typedef struct {
   int candidates;              /* launch shapes timed */
   int row_table;               /* UNFUSED FP32 row kernel: gather table -1 auto, 0 L1, 1 shared memory */
   int row_frames;              /* UNFUSED FP32 row kernel: frames per step (1 or 2) */
+  int batch_persistent;        /* UNFUSED FP32: one persistent launch per call (1) or batched (0) */
 } epic_tune_result;
 
 /* Build the gridding tables of Eq. 9 for every (channel, antenna): the
@@ -188,7 +193,9 @@ epic_status epic_image_host_static(epic_plan_t plan, const void* h_volt, long lo
  * persistent CTA's work unit; UNFUSED: time samples per batch and
  * column-FFT work units per SM, then for FP32 the row kernel's variant:
  * gather table in shared memory or read through L1, one or two frames per
- * step), keeps the fastest in the plan and reports it in *out (may be NULL).  d_image is overwritten; EPICal sums are left
+ * step, and for N = 256 / 512 whether a call runs as one persistent
+ * launch), keeps the fastest in the plan and reports it in *out (may be
+ * NULL).  d_image is overwritten; EPICal sums are left
  * untouched.  Synchronous.  The paper has no counterpart (run-time tuning
  * of this implementation). */
 epic_status epic_autotune(epic_plan_t plan, const void* d_volt, long long n_time, double* d_image,

@@ -52,6 +52,7 @@ class PlanDesc(ct.Structure):
         ("path", ct.c_int),
         ("workspace_bytes", ct.c_size_t),
         ("kernel_param_ant", c_dp),
+        ("batch_persistent", ct.c_int),
     ]
 
 
@@ -71,6 +72,7 @@ class TuneResult(ct.Structure):
         ("path", ct.c_int), ("units_target", ct.c_int), ("batch_time", ct.c_int),
         ("cols_target", ct.c_int), ("ms_default", ct.c_double), ("ms_best", ct.c_double),
         ("candidates", ct.c_int), ("row_table", ct.c_int), ("row_frames", ct.c_int),
+        ("batch_persistent", ct.c_int),
     ]
 
 

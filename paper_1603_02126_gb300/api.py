@@ -58,7 +58,7 @@ class Plan:
 
     def __init__(self, ant_xy_m, freq_hz, grid_n, cell=0.5, kernel="gaussian", support=3,
                  param=0.5, input="ci4", voltage_scale=None, flags=None, stream=None,
-                 path="auto", workspace_bytes=0, precision="fp32"):
+                 path="auto", workspace_bytes=0, precision="fp32", batch_persistent=False):
         lib = B.load()
         self._lib = lib
         self.ant = _f64(ant_xy_m).reshape(-1, 2)
@@ -95,6 +95,7 @@ class Plan:
         d.cuda_stream = ct.c_void_p(int(stream))
         d.path = _PATHS[path]
         d.workspace_bytes = int(workspace_bytes)
+        d.batch_persistent = int(bool(batch_persistent))
         h = ct.c_void_p()
         B.check(lib.epic_plan_create(ct.byref(h), ct.byref(d)))
         self.handle = h

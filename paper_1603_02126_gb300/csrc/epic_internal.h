@@ -266,7 +266,14 @@ struct UnfusedArgs {
   int* err;                // device flag: a bounded wait timed out
   int row_table;           // row kernel's gather table: -1 auto, 0 L1, 1 shared memory
   int row_frames;          // row kernel's frames per step, 1 or 2
+  int sms;                 // SMs of the device (persistent form's work split)
 };
+// One persistent cooperative launch for a whole call (N = 256, 512): rows,
+// grid barrier, columns, grid barrier, correlation, per batch of nt_batch
+// samples.  bar: device {count, generation, abort} (count reset here).
+bool persistent_supported(int n);
+cudaError_t launch_unfused_persistent(const UnfusedArgs& a, long long n_time, int nt_batch, unsigned* bar, int sms,
+                                      cudaStream_t s);
 bool unfused_supported(int n);
 // Lanes per row FFT (N1) of the unfused kernels: absolute column x is gather
 // group j = x / N1 of lane x % N1.

@@ -107,16 +107,13 @@ __device__ __forceinline__ int chan_rs(int R) { return (R + 1) & ~1; }
 // gain multipliers are loaded into registers while this step's rows are
 // transformed.
 template <int N, int NZ, bool TS>
-__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
-    rows_window_kernel(const UnfusedArgs A, long long t0, int nt) {
+__device__ __forceinline__ void rows_body(const UnfusedArgs& A, long long t0, int nt, const float2* tw,
+                                          float2* zbuf, unsigned char* rsm, int cta, int ncta) {
   constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
   constexpr int GROUPS = kUBT / N1, GPW = 32 / N1;
   constexpr int CW = (N2 + 15) / 16;               // uint4 words of group lengths per lane
   constexpr int PF = 2;                            // antennas per thread held for the next step
   using X = fft::Xchg<N1, N2>;
-  __shared__ float2 tw[N];                          // [k2][n1]: e^{+2 pi i n1 k2 / N}
-  __shared__ float2 zbuf[GROUPS * X::ZG];
-  extern __shared__ __align__(16) unsigned char rsm[];
   const int C = A.n_chan, Na = A.n_ant;
   const int F = A.row_frames;
   float2* Es = reinterpret_cast<float2*>(rsm);      // [kRowFrames][Na] E / g of the step's frames
@@ -124,12 +121,11 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
                                                 ~static_cast<size_t>(15)));
   int* sofs = reinterpret_cast<int*>(scnt + static_cast<size_t>(A.rows_alloc) * N1 * CW);
   uint2* sent = reinterpret_cast<uint2*>(sofs + ((A.rows_alloc * N1 + 1) & ~1));
-  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[(i % N1) * (i / N1)];
   const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
   float2* z = zbuf + g * X::ZG;
   const long long frames = static_cast<long long>(nt) * C;
-  const long long per = (frames + gridDim.x - 1) / gridDim.x;
-  const long long ib = static_cast<long long>(blockIdx.x) * per;
+  const long long per = (frames + ncta - 1) / ncta;
+  const long long ib = static_cast<long long>(cta) * per;
   const long long ie = ib + per < frames ? ib + per : frames;
   const bool regpf = Na <= PF * kUBT;
   // the step starting at item `it`: channel, first sample, frames
@@ -275,6 +271,17 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
   }
 }
 
+template <int N, int NZ, bool TS>
+__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
+    rows_window_kernel(const UnfusedArgs A, long long t0, int nt) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2;
+  __shared__ float2 tw[N];                          // [k2][n1]: e^{+2 pi i n1 k2 / N}
+  __shared__ float2 zbuf[(kUBT / N1) * fft::Xchg<N1, N2>::ZG];
+  extern __shared__ __align__(16) unsigned char rsm[];
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[(i % N1) * (i / N1)];
+  rows_body<N, NZ, TS>(A, t0, nt, tw, zbuf, rsm, blockIdx.x, gridDim.x);   // its first step syncs
+}
+
 // Bounded wait of one thread on an mbarrier phase; false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
   for (int i = 0; i < (1 << 22); ++i) {
@@ -304,35 +311,26 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 // the slot's mbarrier (bounded), then a CTA barrier hands the slot to all
 // warps.  N = 512 reads the columns from global memory (the two slots and
 // the FFT exchange would not leave room for two CTAs per SM).
-template <int N, int NZ, bool STAGE>
-__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(const UnfusedArgs A, int nt, int segs) {
+// COH (persistent form): the spectra were written by other SMs earlier in
+// the same launch, so they are read around L1 (ld.global.cg), and image
+// updates are atomics (the unit-to-CTA mapping may change between batches).
+template <int N, int NZ, bool STAGE, bool COH = false>
+__device__ __forceinline__ bool cols_body(const UnfusedArgs& A, int nt, int segs, const float2* tw, float2* zbuf,
+                                          float2* slot, uint64_t* bars, volatile int* abort_flag,
+                                          uint32_t (&uses)[2], int cta, int ncta) {
   constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2, H = N2 / N1;
   constexpr int GROUPS = kUBT / N1;
   constexpr int CBLK = (N + GROUPS - 1) / GROUPS;   // column blocks per channel
   constexpr int NCOL = N < GROUPS ? N : GROUPS;     // columns per block
   using X = fft::Xchg<N1, N2>;
-  __shared__ float2 tw[N];
-  __shared__ float2 zbuf[GROUPS * X::ZG];
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ int abort_flag;
-  extern __shared__ __align__(128) float2 slot[];   // [2][NCOL][rs]
-  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[(i % N1) * (i / N1)];
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + s)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    abort_flag = 0;
-  }
-  __syncthreads();
   const int g = threadIdx.x / N1, n1 = threadIdx.x % N1;
   const int lane = threadIdx.x & 31;
   const unsigned gmask = fft::group_mask<N1>(lane);
   float2* z = zbuf + g * X::ZG;
   const int C = A.n_chan, rs = A.rs;                // frame stride N * rs
   const int units = C * CBLK * segs;
-  uint32_t uses[2] = {0u, 0u};                     // completed phases per slot (thread 0)
   bool ok = true;
-  for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+  for (int u = cta; u < units && ok; u += ncta) {
     const int s = u % segs;
     const int cb = (u / segs) % CBLK;
     const int c = u / (segs * CBLK);
@@ -365,13 +363,13 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(c
                       smem_addr(bars + (sl ^ 1)));
           }
           if (!mbar_wait_bounded(smem_addr(bars + sl), uses[sl] & 1u)) {
-            abort_flag = 1;
+            *abort_flag = 1;
             atomicExch(A.err, 1);
           }
           ++uses[sl];
         }
         __syncthreads();
-        if (abort_flag) {
+        if (*abort_flag) {
           ok = false;
           break;
         }
@@ -383,7 +381,8 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(c
 #pragma unroll
         for (int j = 0; j < N2; ++j) {
           const int jw = n1 + N1 * j;
-          v[j] = (j < NZ && jw < R) ? (STAGE ? col[jw] : __ldcs(col + jw)) : make_float2(0.f, 0.f);
+          v[j] = (j < NZ && jw < R) ? (STAGE ? col[jw] : (COH ? __ldcg(col + jw) : __ldcs(col + jw)))
+                                    : make_float2(0.f, 0.f);
         }
         fft::fft_lanes_p<N1, N2, NZ>(v, n1, z, tw, gmask);
 #pragma unroll
@@ -404,35 +403,54 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(c
       for (int k1 = 0; k1 < N1; ++k1) {
         const int ky = n1 + N1 * h + N2 * k1;
         const double v = static_cast<double>(acc[h * N1 + k1]) * A.img_scale;
-        if (segs == 1) img[ky * N + kx] += v;
+        if (segs == 1 && !COH) img[ky * N + kx] += v;
         else atomicAdd(img + ky * N + kx, v);
       }
   }
   // after a timeout: let this thread's copies still in flight land (bounded)
-  if (!ok && threadIdx.x == 0)
+  if (STAGE && !ok && threadIdx.x == 0)
     for (int sl = 0; sl < 2; ++sl) mbar_wait_bounded(smem_addr(bars + sl), uses[sl] & 1u);
+  return ok;
+}
+
+template <int N, int NZ, bool STAGE>
+__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2)) cols_window_kernel(const UnfusedArgs A, int nt, int segs) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[(kUBT / N1) * fft::Xchg<N1, N2>::ZG];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int abort_flag;
+  extern __shared__ __align__(128) float2 slot[];   // [2][NCOL][rs]
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[(i % N1) * (i / N1)];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + s)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  uint32_t uses[2] = {0u, 0u};                     // completed phases per slot (thread 0)
+  cols_body<N, NZ, STAGE>(A, nt, segs, tw, zbuf, slot, bars, &abort_flag, uses, blockIdx.x, gridDim.x);
 }
 
 // ---- EPICal correlation: one thread per (channel, antenna, time segment) ----
-__global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
+__device__ __forceinline__ void corr_item(const UnfusedArgs& A, long long t0, int nt, int i, int sy, int nsy) {
   const int Na = A.n_ant, C = A.n_chan;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= C * Na) return;
   const int c = i / Na, a = i % Na;
   if (__ldg(A.cell0 + i) < 0) return;
   const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
-  const int tb = nt * blockIdx.y / gridDim.y, te = nt * (blockIdx.y + 1) / gridDim.y;
+  const int tb = nt * sy / nsy, te = nt * (sy + 1) / nsy;
   float kr = 0.f, ki = 0.f, pp = 0.f;
   for (int tl = tb; tl < te; ++tl) {
     const size_t f = static_cast<size_t>(tl) * C + c;
-    const float2 p = A.pix[f];
+    const float2 p = __ldcg(A.pix + f);            // written by another SM (persistent form)
     const float2 e0 = load_volt_u(A.volt, A.input_fmt, (static_cast<size_t>(t0 + tl) * C + c) * Na + a);
     const float2 e = make_float2(e0.x * vs, e0.y * vs);
     kr += e.x * p.x + e.y * p.y;
     ki += e.y * p.x - e.x * p.y;
     pp += e.x * e.x + e.y * e.y;
   }
-  if (gridDim.y == 1) {
+  if (nsy == 1) {
     A.kacc[i].x += kr;
     A.kacc[i].y += ki;
     A.pacc[i] += pp;
@@ -443,6 +461,12 @@ __global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
   }
 }
 
+__global__ void correlate_kernel(const UnfusedArgs A, long long t0, int nt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.n_chan * A.n_ant) return;
+  corr_item(A, t0, nt, i, blockIdx.y, gridDim.y);
+}
+
 // Time segments for the correlation: enough blocks to fill the GPU, at
 // least 16 time samples each.
 dim3 correlate_grid(int n_chan, int n_ant, int nt, int sms) {
@@ -450,6 +474,122 @@ dim3 correlate_grid(int n_chan, int n_ant, int nt, int sms) {
   int sy = 1;
   while (bx * sy < 4 * sms && nt / (2 * sy) >= 16) sy *= 2;
   return dim3(static_cast<unsigned>(bx), static_cast<unsigned>(sy));
+}
+
+// Grid-wide barrier of the persistent form (all CTAs co-resident: a
+// cooperative launch).  Thread 0 of every CTA reads the generation, arrives
+// on the counter; the last arriver resets the counter and advances the
+// generation, the others wait for it with a bounded number of polls, after
+// which the kernel's abort flag and the plan's error flag are raised and
+// every CTA stops.  bar = {count, generation}.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vabort = bar + 2;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = *vabort == 0u;
+    if (ok) {
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        int i = 0;
+        for (; i < (1 << 22) && *vgen == g && *vabort == 0u; ++i) __nanosleep(64);
+        if (*vgen == g) {
+          ok = 0;
+          atomicExch(bar + 2, 1u);
+          atomicExch(err, 1);
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// One launch for a whole epic_image call on the plain path: for every batch
+// of samples the row phase, a grid barrier, the column phase, a grid
+// barrier, the correlation phase (its result is read by no one before the
+// next batch's column phase, two barriers later).  Gather tables through L1,
+// column loads from global memory: the row and column phases then need the
+// same shared memory (twiddles, FFT exchange) and fit side by side.
+template <int N, int NZR, int NZC>
+__global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
+    unfused_persistent_kernel(const UnfusedArgs A, long long n_time, int nt_batch, unsigned* bar) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2;
+  constexpr int GROUPS = kUBT / N1;
+  constexpr int CBLK = (N + GROUPS - 1) / GROUPS;
+  __shared__ float2 tw[N];
+  __shared__ float2 zbuf[GROUPS * fft::Xchg<N1, N2>::ZG];
+  extern __shared__ __align__(16) unsigned char rsm[];
+  for (int i = threadIdx.x; i < N; i += kUBT) tw[i] = A.twid[(i % N1) * (i / N1)];
+  __syncthreads();
+  __shared__ int unused_abort;
+  uint32_t uses[2] = {0u, 0u};
+  const int C = A.n_chan, Na = A.n_ant;
+  for (long long t0 = 0; t0 < n_time; t0 += nt_batch) {
+    const int nt = static_cast<int>(n_time - t0 < nt_batch ? n_time - t0 : nt_batch);
+    rows_body<N, NZR, false>(A, t0, nt, tw, zbuf, rsm, blockIdx.x, gridDim.x);
+    if (!grid_barrier(bar, A.err)) return;
+    int segs = 1;
+    while (C * CBLK * segs < A.cols_target * A.sms && segs * 8 <= nt) segs *= 2;
+    cols_body<N, NZC, false, true>(A, nt, segs, tw, zbuf, nullptr, nullptr, &unused_abort, uses, blockIdx.x,
+                                   gridDim.x);
+    if (!grid_barrier(bar, A.err)) return;
+    if (A.do_cal) {
+      const int bx = (C * Na + 255) / 256;
+      int sy = 1;
+      while (bx * sy < 4 * A.sms && nt / (2 * sy) >= 16) sy *= 2;
+      const long long items = static_cast<long long>(C) * Na * sy;
+      for (long long k = static_cast<long long>(blockIdx.x) * kUBT + threadIdx.x; k < items;
+           k += static_cast<long long>(gridDim.x) * kUBT)
+        corr_item(A, t0, nt, static_cast<int>(k % (C * Na)), static_cast<int>(k / (C * Na)), sy);
+    }
+  }
+}
+
+template <int N, int NZR, int NZC>
+cudaError_t persistent_launch(const UnfusedArgs& a, long long n_time, int nt_batch, unsigned* bar, int sms,
+                              cudaStream_t s) {
+  const size_t es = static_cast<size_t>(kRowFrames) * a.n_ant * sizeof(float2);
+  auto kern = unfused_persistent_kernel<N, NZR, NZC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(es));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kUBT, es);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);   // count, generation, abort
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(per_sm * sms));
+  cfg.blockDim = dim3(kUBT);
+  cfg.dynamicSmemBytes = es;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a, n_time, nt_batch, bar);
+}
+
+template <int N>
+cudaError_t launch_persistent_n(const UnfusedArgs& a, long long n_time, int nt_batch, unsigned* bar, int sms,
+                                cudaStream_t s) {
+  constexpr int N1 = UCfg<N>::N1, N2 = UCfg<N>::N2;
+  if (a.max_cols <= N1 * (N2 / 2)) {
+    if (a.rows_alloc <= N1 * (N2 / 2)) return persistent_launch<N, N2 / 2, N2 / 2>(a, n_time, nt_batch, bar, sms, s);
+    return persistent_launch<N, N2 / 2, N2>(a, n_time, nt_batch, bar, sms, s);
+  }
+  if (a.rows_alloc <= N1 * (N2 / 2)) return persistent_launch<N, N2, N2 / 2>(a, n_time, nt_batch, bar, sms, s);
+  return persistent_launch<N, N2, N2>(a, n_time, nt_batch, bar, sms, s);
 }
 
 template <int N, int NZ, bool TS>
@@ -550,6 +690,17 @@ int unfused_fft_lanes(int n) {
 cudaError_t launch_correlate(const UnfusedArgs& a, long long t0, int nt, cudaStream_t s) {
   correlate_kernel<<<correlate_grid(a.n_chan, a.n_ant, nt, 152), 256, 0, s>>>(a, t0, nt);
   return cudaGetLastError();
+}
+
+bool persistent_supported(int n) { return n == 256 || n == 512; }
+
+cudaError_t launch_unfused_persistent(const UnfusedArgs& a, long long n_time, int nt_batch, unsigned* bar, int sms,
+                                      cudaStream_t s) {
+  switch (a.grid_n) {
+    case 256: return launch_persistent_n<256>(a, n_time, nt_batch, bar, sms, s);
+    case 512: return launch_persistent_n<512>(a, n_time, nt_batch, bar, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_unfused_batch(const UnfusedArgs& a, long long t0, int nt, int sms, cudaStream_t s) {

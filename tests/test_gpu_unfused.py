@@ -90,3 +90,57 @@ def test_unfused_epical_interval_matches_oracle():
     amp = np.max(np.abs(np.abs(g) - np.abs(g_ref)) / np.abs(g_ref))
     ph = np.max(np.abs(np.angle(g * np.conj(g_ref))))
     assert amp <= GAIN_TOL and ph <= GAIN_TOL, (amp, ph)
+
+
+@pytest.mark.parametrize("n,na,diam,C,T", [(256, 300, 150.0, 2, 9), (512, 600, 300.0, 2, 7)])
+def test_persistent_launch_matches_oracle_and_batched(n, na, diam, C, T):
+    """One persistent cooperative launch per call (row phase, grid barrier,
+    column phase, grid barrier, correlation, for every batch): image and an
+    EPICal interval against the oracle and against the batched launches,
+    with a scratch small enough for several batches per call; then the same
+    interval captured in a CUDA graph and replayed."""
+    from paper_1603_02126_gb300 import Plan
+    rng = np.random.default_rng(700 + n)
+    ant = synth.layout_disc(na, diam, rng, 0.5)
+    freqs = np.linspace(45e6, 62e6, C)
+    flags = np.zeros(na, bool)
+    flags[[5, 77]] = True
+    sky = np.array([[0.0, 0.0, 5.0], [0.1, -0.2, 3.0], [-0.3, 0.3, 1.0]])
+    E = synth.voltages(ant, freqs, synth.true_gains(C, na, rng), sky, T, 1.0, rng)
+    lsb = np.full(C, 0.6)
+    b = synth.quantise_ci4(E, lsb)
+    Eint = O.unpack_ci4(b) * lsb[None, :, None]
+    d = torch.from_numpy(b).cuda()
+    ws = 3 * C * n * (n // 2 + 8) * 8                    # about 3 samples per batch
+    kw = dict(support=3, param=0.5, input="ci4", voltage_scale=lsb, flags=flags, path="unfused",
+              workspace_bytes=ws)
+    outs = []
+    for pers in (True, False):
+        p = Plan(ant, freqs, n, 0.5, batch_persistent=pers, **kw)
+        p.configure((0.0, 0.0), sky, 0.5)
+        img = p.image(d).cpu().numpy()
+        g = torch.zeros((C, na), dtype=torch.complex128, device="cuda")
+        p.update(g)
+        assert p.sync() == 0
+        assert p.info()["batch_time"] < T                 # several batches per call
+        outs.append((img, g.cpu().numpy(), p))
+    oplan = O.Plan(ant, freqs, n, 0.5, flags=flags, model_lmS=sky)
+    ref, _ = O.image_interval(oplan, Eint, np.ones((C, na), complex), block=4)
+    assert _rel(outs[0][0], ref) <= IMG_TOL
+    assert _rel(outs[0][0], outs[1][0]) <= 1e-6
+    g_ref, *_ = O.epical_interval(oplan, Eint, np.ones((C, na), complex), 0.5, with_image=False)
+    ok = ~flags
+    amp = np.max(np.abs(np.abs(outs[0][1][:, ok]) - np.abs(g_ref[:, ok])) / np.abs(g_ref[:, ok]))
+    ph = np.max(np.abs(np.angle(outs[0][1][:, ok] * np.conj(g_ref[:, ok]))))
+    assert amp <= 1e-4 and ph <= 1e-4, (amp, ph)
+    # the persistent interval inside a CUDA graph
+    p = outs[0][2]
+    stream = torch.cuda.Stream()
+    p.set_stream(stream.cuda_stream)
+    img_g = torch.empty((C, n, n), dtype=torch.float64, device="cuda")
+    p.graph_capture(d, img_g)
+    p.graph_launch()
+    torch.cuda.synchronize()
+    # the replay images with the gains of the first update
+    ref1, _ = O.image_interval(oplan, Eint, outs[0][1], block=4)
+    assert _rel(img_g.cpu().numpy(), ref1) <= IMG_TOL
