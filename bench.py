@@ -287,15 +287,25 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
     p3b.graph_capture(v3, img3, g3)
     p3b.graph_launch()
     ms_b3 = run(p3b.graph_launch, 2)
+    # one persistent cooperative launch per interval (+ the update) in a graph
+    p3p = Plan(w3["ant_xy"], w3["freqs"], 512, 0.5, path="unfused", workspace_bytes=8 << 30,
+               batch_persistent=True, **kw3)
+    p3p.configure((0.0, 0.0), w3["model"], w3["gamma"])
+    p3p.graph_capture(v3, img3, g3)
+    p3p.graph_launch()
+    ms_pg3 = run(p3p.graph_launch, 2)
     out["hex2048_n512"] = {
         "workload": "Na=2048 hexagonal 8 m pitch +-0.5 m jitter, C=256 ch 50-100 MHz, N=512, "
                     "T=4096 complex64, EPICal armed",
         "plain_fp32": {"ms": ms_p3, "frames_per_s": frames3 / ms_p3 * 1e3},
         "batched_graph_autotuned": {"ms": ms_b3, "frames_per_s": frames3 / ms_b3 * 1e3,
                                     "speedup_vs_plain": ms_p3 / ms_b3, "tune": tune3},
+        "persistent_graph": {"ms": ms_pg3, "frames_per_s": frames3 / ms_pg3 * 1e3,
+                             "speedup_vs_plain": ms_p3 / ms_pg3, "launches_per_interval": 2},
     }
     p3.close()
     p3b.close()
+    p3p.close()
     del v3, img3
 
     # -- differentiation: Na=256, N=128, C=16, T=4096; chi^2 to the 50-source model image
@@ -331,6 +341,22 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
     g_adam = solve_gains(p4, v4, M, g0, steps=60, lr=0.01, decay=0.97)
     torch.cuda.synchronize()
     adam_s = time.perf_counter() - t0
+    # the BF16 option of the adjoint's transforms: gradient vs the FP32 one
+    # (itself within 1e-4 of the FP64 oracle in the tests), timing, solve
+    def grad_at(prec):
+        p4.set_adjoint_precision(prec)
+        g = g_true.clone().requires_grad_(True)
+        chi2(EpicImageFn.apply(g, v4, p4), M).backward()
+        return g.grad
+
+    gr32, gr16 = grad_at("fp32"), grad_at("bf16")
+    bf16_grad_err = float(torch.linalg.norm(gr16 - gr32) / torch.linalg.norm(gr32))
+    ms_fb16 = run(fwd_bwd, reps)
+    t0 = time.perf_counter()
+    g_adam16 = solve_gains(p4, v4, M, g0, steps=60, lr=0.01, decay=0.97)
+    torch.cuda.synchronize()
+    adam16_s = time.perf_counter() - t0
+    p4.set_adjoint_precision("fp32")
     pe = Plan(w4["ant_xy"], w4["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
               voltage_scale=w4["lsb"], stream=sc)
     pe.configure((0.0, 0.0), w4["model"], w4["gamma"], g0=w4["gains"] * pert)
@@ -353,6 +379,9 @@ def forms(torch, Plan, dev, stream, flush, w1, volt1, steps):
                     "model image",
         "forward_ms": ms_f, "forward_backward_ms": ms_fb,
         "adam_60_steps": {"s": adam_s, "ms_per_step": adam_s / 60 * 1e3, "sigma_g": sig(g_adam.cpu().numpy())},
+        "bf16_adjoint": {"forward_backward_ms": ms_fb16, "backward_speedup": (ms_fb - ms_f) / (ms_fb16 - ms_f),
+                         "grad_rel_l2_vs_fp32": bf16_grad_err,
+                         "adam_60_steps": {"s": adam16_s, "sigma_g": sig(g_adam16.cpu().numpy())}},
         "epical_60_loops": {"s": epical_s, "sigma_g": sig(pe.gains())},
         "sigma_g_start": sig(w4["gains"] * pert),
     }

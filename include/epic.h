@@ -405,6 +405,16 @@ epic_status epic_set_gains_device(epic_plan_t plan, const double* d_gains);
 epic_status epic_image_backward(epic_plan_t plan, const void* d_volt, long long n_time,
                                 const double* d_dl_di, double* d_grad_g);
 
+/* Arithmetic of the transforms in epic_image_backward: EPIC_PREC_FP32 (the
+ * default) or EPIC_PREC_BF16, where two frames at a time go through the
+ * four FFTs, the multiply by R and the shared-memory exchanges as BF16
+ * pairs (gridding sums, degridding sums, the conj(E_a) products and the
+ * accumulation stay FP32, the gradient sums FP64).  The BF16 gradient
+ * carries the rounding of 8-bit significands through about 4 log2(N)
+ * butterfly levels (a relative error of order 10^-2).  Host only; applies
+ * to later calls.  Errors: INVALID_ARG (another precision). */
+epic_status epic_plan_set_adjoint_precision(epic_plan_t plan, int precision);
+
 /* Debug/test accessors (synchronous, host outputs). */
 /* base_xy: host [C][Na][2] int32 stencil-centre cell (x, y); w: host
  * [C][Na][K][K] float64 normalised tap weights ([dy][dx]); either may be

@@ -30,7 +30,7 @@ EXPORTS = [
     "epic_set_gains_device", "epic_image_backward", "epic_autotune", "epic_graph_capture",
     "epic_graph_launch", "epic_measure_fma_peak", "epical_configure_pixels",
     "epical_get_direction_gains", "epic_visibilities", "epic_visibility_solve", "epical_fit_bandpass",
-    "epic_set_phase_centre", "epic_plan_set_wait_limit",
+    "epic_set_phase_centre", "epic_plan_set_wait_limit", "epic_plan_set_adjoint_precision",
 ]
 
 c_dp = ct.POINTER(ct.c_double)
@@ -127,6 +127,7 @@ def load(path: str | None = None) -> ct.CDLL:
         "epical_fit_bandpass": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_int],
         "epic_set_phase_centre": [P, ct.c_double, ct.c_double],
         "epic_plan_set_wait_limit": [P, ct.c_int],
+        "epic_plan_set_adjoint_precision": [P, ct.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

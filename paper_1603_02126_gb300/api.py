@@ -215,6 +215,14 @@ class Plan:
                                               _dptr(grad, torch.complex128, "grad")))
         return grad
 
+    def set_adjoint_precision(self, precision):
+        """Arithmetic of image_backward's transforms: "fp32" or "bf16"
+        (two frames at a time as BF16 pairs)."""
+        code = {"fp32": B.EPIC_PREC_FP32, "bf16": B.EPIC_PREC_BF16}.get(precision)
+        if code is None:
+            raise ValueError(f"adjoint precision must be 'fp32' or 'bf16', not {precision!r}")
+        B.check(self._lib.epic_plan_set_adjoint_precision(self.handle, code))
+
     def autotune(self, volt, image=None) -> dict:
         """Time launch-shape candidates on this batch and keep the fastest."""
         torch = _torch()

@@ -21,9 +21,10 @@ LIB = os.path.join(OUT, "libepic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["epic_kernels.cu", "epic_unfused.cu", "epic_tc.cu", "epic_cluster.cu", "epic_noalloc.cu",
-              "epic_piped.cu", "epic_peak.cu", "epic_multipix.cu", "epic_xengine.cu"]
+              "epic_piped.cu", "epic_peak.cu", "epic_multipix.cu", "epic_xengine.cu", "epic_adjoint.cu"]
 CXX_SOURCES = ["epic_plan.cpp"]
 HEADERS = [os.path.join(CSRC, "epic_internal.h"), os.path.join(CSRC, "epic_fft.cuh"),
+           os.path.join(CSRC, "epic_fused_geo.cuh"),
            os.path.join(ROOT, "include", "epic.h")]
 
 

@@ -152,7 +152,8 @@ int image_rs_fused(int rows_alloc);
 
 // Dynamic shared memory of the adjoint kernel (layout: window [rows][N],
 // spectra [N][rs], FFT exchange, twiddles, E' [Na]).
-size_t adjoint_smem_bytes(int n, int rows_alloc, int rs, int n_ant);
+// Dynamic shared memory of the adjoint kernel (bf16: the BF16 frame-pair form).
+size_t adjoint_smem_bytes(int n, int rows_alloc, int rs, int n_ant, bool bf16);
 // Row stride of the fused kernel's grid window, N + N1.
 int image_window_stride(int n);
 size_t image_smem_bytes(int n, int n_ant, int rs, int steps);
@@ -218,7 +219,9 @@ struct AdjointArgs {
   int segs, rows_alloc, rs, grid;
   size_t smem;
 };
-cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s);
+// bf16: spectra of two frames at a time as BF16 pairs (FP32 gridding,
+// degridding and accumulation), else FP32 throughout.
+cudaError_t launch_adjoint(int n, const AdjointArgs& a, bool bf16, cudaStream_t s);
 // phase: [C][Na] phasing factors p (the multiplier is w = p / g), or nullptr.
 cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
                                     const double2* phase, const unsigned char* flags, double2* out,

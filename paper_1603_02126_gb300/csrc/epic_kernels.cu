@@ -25,6 +25,7 @@
 // N1-point DFTs (the four-step decomposition).  Twiddles come from an FP64
 // host table rounded to float.
 #include "epic_fft.cuh"
+#include "epic_fused_geo.cuh"
 #include "epic_internal.h"
 
 #include <cstdint>
@@ -38,61 +39,7 @@ using fft::csub;
 using fft::Dft;
 using fft::kFull;
 
-// Per-N launch shape: N1 lanes per 1-D FFT, N2 points per lane, BT threads.
-template <int N> struct Cfg;
-template <> struct Cfg<16>  { static constexpr int N1 = 4, N2 = 4,  BT = 64; };
-template <> struct Cfg<32>  { static constexpr int N1 = 4, N2 = 8,  BT = 128; };
-template <> struct Cfg<64>  { static constexpr int N1 = 8, N2 = 8,  BT = 512; };
-template <> struct Cfg<128> { static constexpr int N1 = 8, N2 = 16, BT = 512; };
-
-constexpr int kMaxAntPerThread = 4;
 constexpr double kPiD = 3.14159265358979323846;
-
-template <int N>
-struct Geo {
-  static constexpr int N1 = Cfg<N>::N1, N2 = Cfg<N>::N2, BT = Cfg<N>::BT;
-  static constexpr int GROUPS = BT / N1;
-  static constexpr int COLROUNDS = N / GROUPS;
-  static constexpr int NACC = COLROUNDS * N2;
-  static constexpr int H = N2 / N1;
-  static constexpr int ZS = N1 + 1;                       // padded exchange row
-  static constexpr int ZG0 = N2 * ZS;
-  static constexpr int ZG = ZG0 + ((8 - ZG0 % 16) + 16) % 16;  // group stride
-  static_assert(N1 * N2 == N, "N1*N2 must be N");
-  static_assert(N2 % N1 == 0, "N2 must be a multiple of N1");
-  static_assert(N % GROUPS == 0, "columns must split evenly over groups");
-  static_assert(32 % N1 == 0, "FFT groups must tile a warp");
-};
-
-// 1-D FFT of length N on a group of N1 lanes (see fft::fft_lanes).
-template <int N>
-__device__ __forceinline__ void fft_group(float2 (&v)[Geo<N>::N2], int n1, float2* z,
-                                          const float2* tw, unsigned gmask) {
-  fft::fft_lanes<Geo<N>::N1, Geo<N>::N2>(v, n1, z, tw, gmask);
-}
-
-__device__ __forceinline__ float2 load_volt(const void* volt, int fmt, int n_chan, int n_ant,
-                                           long long t, int c, int a) {
-  const size_t idx = (static_cast<size_t>(t) * n_chan + c) * n_ant + a;
-  if (fmt == 0) {
-    const unsigned b = __ldg(static_cast<const unsigned char*>(volt) + idx);
-    const int re = static_cast<int>(b << 24) >> 28;
-    const int im = static_cast<int>(b << 28) >> 28;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-  }
-  return __ldg(static_cast<const float2*>(volt) + idx);
-}
-
-__device__ __forceinline__ float2 load_volt(const ImageArgs& A, long long t, int c, int a) {
-  const size_t idx = (static_cast<size_t>(t) * A.n_chan + c) * A.n_ant + a;
-  if (A.input_fmt == 0) {
-    const unsigned b = __ldg(static_cast<const unsigned char*>(A.volt) + idx);
-    const int re = static_cast<int>(b << 24) >> 28;
-    const int im = static_cast<int>(b << 28) >> 28;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-  }
-  return __ldg(static_cast<const float2*>(A.volt) + idx);
-}
 
 // Raw voltage of antenna a in frame t, fetched one frame ahead: the 4-bit
 // byte (ci4) or the complex64 value, unpacked only when it is used.
@@ -463,221 +410,6 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_fused(const ImageArg
   }
 }
 
-// Adjoint of the imaging chain (differentiation form).  With R = dL/dI for
-// the dirty image I, X(t) the raw FFT of the folded grid of frame t, and
-// W'_a the folded stencil weights, the gradient of L with respect to the
-// conjugate gain multipliers is
-//   dL/dconj(w_a) = (1/T) sum_t conj(E_a(t)) sum_j W'_a(j) [F^- (R . X(t))]_j
-// (F^- = the conjugate transform).  Every frame is recomputed (nothing is
-// stored): gridding as a per-lane gather from E' in shared memory (the plan's
-// absolute-column tap lists) straight into the row FFTs, column FFTs,
-// multiply by R, inverse column FFTs into the grid window, inverse row FFTs,
-// degridding gather of the K x K taps per antenna.  E' of the next frame is
-// formed during the degridding.  R for the unit's channel stays in registers.
-template <int N, int MAXA>
-__global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint(const AdjointArgs A) {
-  using G = Geo<N>;
-  constexpr int BT = G::BT, N1 = G::N1, N2 = G::N2, GROUPS = G::GROUPS, H = G::H;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Wg = reinterpret_cast<float2*>(smem_raw);   // [rows_alloc][N]
-  float2* Tt = Wg + A.rows_alloc * N;                  // [N][rs] or [rows][N]
-  float2* Z = Tt + N * A.rs;
-  float2* tw = Z + GROUPS * G::ZG;
-  float2* Es = tw + N;                                 // [Na] E / g of the current frame
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int g = tid / N1;
-  const int n1 = tid % N1;
-  const unsigned gmask = fft::group_mask<N1>(lane);
-  float2* zg = Z + g * G::ZG;
-
-  for (int i = tid; i < N; i += BT) tw[i] = A.twid[i];
-  __syncthreads();
-
-  const int Na = A.n_ant;
-  const int K = A.support;
-  const int KK = K * K;
-  const long long T = A.n_time;
-  const int units = A.n_chan * A.segs;
-
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
-    const int c = u / A.segs;
-    const int s = u - c * A.segs;
-    const long long t0 = T * s / A.segs;
-    const long long t1 = T * (s + 1) / A.segs;
-    if (t0 >= t1) continue;
-    const int2 wn = __ldg(A.win + c);
-    const int y0 = wn.x, R = wn.y;
-    const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
-    const int* cell0 = A.cell0 + static_cast<size_t>(c) * Na;
-    const float* wts = A.wts + static_cast<size_t>(c) * Na * KK;
-    const float2* wg = A.wgain + static_cast<size_t>(c) * Na;
-    const double* rimg = A.dldi + static_cast<size_t>(c) * N * N;
-    const int* gofs = A.gofs + static_cast<size_t>(c) * A.rows_alloc * N1;
-    const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * N1;
-    const uint2* gent = A.gent + __ldg(A.gbase + c);
-
-    // R_k for this thread's pixels, in the column-FFT output order
-    float rk[G::NACC];
-#pragma unroll
-    for (int r = 0; r < G::COLROUNDS; ++r) {
-      const int kx = g + GROUPS * r;
-#pragma unroll
-      for (int h = 0; h < H; ++h)
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const int ky = n1 + N1 * h + N2 * k1;
-          rk[r * N2 + h * N1 + k1] = static_cast<float>(__ldg(rimg + ky * N + kx));
-        }
-    }
-    // raw voltages (scaled) of the unit's first frame and its E' = E / g
-    float2 gac[MAXA], ecur[MAXA];
-#pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      const int a = tid + BT * i;
-      gac[i] = make_float2(0.f, 0.f);
-      ecur[i] = make_float2(0.f, 0.f);
-      if (a < Na) {
-        const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t0, c, a);
-        ecur[i] = make_float2(e.x * vs, e.y * vs);
-        Es[a] = cmul(ecur[i], __ldg(wg + a));
-      }
-    }
-    __syncthreads();
-
-    for (long long t = t0; t < t1; ++t) {
-      // ---- B: gridding gather (Eq. 9, absolute columns n1 + N1 j) + row FFTs ----
-      for (int row = g; row < R; row += GROUPS) {
-        float2 v[N2];
-        {
-          const int li = row * N1 + n1;
-          int e = __ldg(gofs + li);
-          const uint4 cw = __ldg(gcnt + li);
-          const unsigned cv[4] = {cw.x, cw.y, cw.z, cw.w};
-#pragma unroll
-          for (int j = 0; j < N2; ++j) {
-            const int cj = static_cast<int>((cv[j >> 2] >> (8 * (j & 3))) & 255u);
-            float2 sum = make_float2(0.f, 0.f);
-            for (int k = 0; k < cj; ++k) {
-              const uint2 en = __ldg(gent + e + k);
-              const float2 x = Es[en.x];
-              const float w = __uint_as_float(en.y);
-              sum.x = fmaf(w, x.x, sum.x);
-              sum.y = fmaf(w, x.y, sum.y);
-            }
-            e += cj;
-            v[j] = sum;
-          }
-        }
-        fft_group<N>(v, n1, zg, tw, gmask);
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) Tt[(n1 + N1 * h + N2 * k1) * A.rs + row] = v[h * N1 + k1];
-      }
-      __syncthreads();
-
-      // ---- C: column FFTs, multiply by R, inverse column FFTs into the window ----
-#pragma unroll
-      for (int r = 0; r < G::COLROUNDS; ++r) {
-        const int kx = g + GROUPS * r;
-        float2 v[N2];
-#pragma unroll
-        for (int j = 0; j < N2; ++j) {
-          const int jw = n1 + N1 * j - y0;
-          v[j] = (jw >= 0 && jw < R) ? Tt[kx * A.rs + jw] : make_float2(0.f, 0.f);
-        }
-        fft_group<N>(v, n1, zg, tw, gmask);
-        // output slot h*N1 + k1 holds ky = n1 + N1*(h + H*k1): the inverse
-        // transform's input slot j = h + H*k1; conjugate for F^-
-        float2 u[N2];
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const float rv = rk[r * N2 + h * N1 + k1];
-            const float2 x = v[h * N1 + k1];
-            u[h + H * k1] = make_float2(x.x * rv, -x.y * rv);
-          }
-        fft_group<N>(u, n1, zg, tw, gmask);
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const int jw = n1 + N1 * h + N2 * k1 - y0;
-            if (jw >= 0 && jw < R) {
-              const float2 x = u[h * N1 + k1];
-              Wg[jw * N + kx] = make_float2(x.x, -x.y);
-            }
-          }
-      }
-      __syncthreads();
-
-      // ---- D: inverse row FFTs of the window rows, row-major into Tt ----
-      for (int row = g; row < R; row += GROUPS) {
-        float2 v[N2];
-        float2* wr = Wg + row * N;
-#pragma unroll
-        for (int j = 0; j < N2; ++j) {
-          const float2 x = wr[n1 + N1 * j];
-          v[j] = make_float2(x.x, -x.y);
-        }
-        fft_group<N>(v, n1, zg, tw, gmask);
-#pragma unroll
-        for (int h = 0; h < H; ++h)
-#pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) {
-            const float2 x = v[h * N1 + k1];
-            Tt[row * N + n1 + N1 * h + N2 * k1] = make_float2(x.x, -x.y);
-          }
-      }
-      __syncthreads();
-
-      // ---- E: degrid and accumulate conj(E_a) Y_a ----
-#pragma unroll
-      for (int i = 0; i < MAXA; ++i) {
-        const int a = tid + BT * i;
-        if (a < Na) {
-          const int c0 = __ldg(cell0 + a);
-          if (c0 >= 0) {
-            const float* wa = wts + static_cast<size_t>(a) * KK;
-            float yr = 0.f, yi = 0.f;
-            for (int dy = 0; dy < K; ++dy)
-              for (int dx = 0; dx < K; ++dx) {
-                const float w = __ldg(wa + dy * K + dx);
-                const float2 b = Tt[c0 + dy * N + dx];
-                yr += w * b.x;
-                yi += w * b.y;
-              }
-            const float2 e = ecur[i];
-            gac[i].x += e.x * yr + e.y * yi;     // conj(e) * y
-            gac[i].y += e.x * yi - e.y * yr;
-          }
-          // next frame's raw voltages and E' (the row pass reads Es after the barrier)
-          if (t + 1 < t1) {
-            const float2 e = load_volt(A.volt, A.input_fmt, A.n_chan, Na, t + 1, c, a);
-            ecur[i] = make_float2(e.x * vs, e.y * vs);
-            Es[a] = cmul(ecur[i], __ldg(wg + a));
-          }
-        }
-      }
-      __syncthreads();                                 // Tt and Es are rewritten next frame
-    }
-#pragma unroll
-    for (int i = 0; i < MAXA; ++i) {
-      const int a = tid + BT * i;
-      if (a < Na && cell0[a] >= 0) {
-        const size_t o = static_cast<size_t>(c) * Na + a;
-        atomicAdd(&A.dldw[o].x, static_cast<double>(gac[i].x) * A.img_scale);
-        atomicAdd(&A.dldw[o].y, static_cast<double>(gac[i].y) * A.img_scale);
-      }
-    }
-  }
-}
-
-// grad = 2 dL/dconj(g) = 2 dL/dconj(w) * (-1 / conj(g)^2); flagged -> 0.
 // Multiplier of Eq. 8 with the phasing of the plan's phase centre:
 // w = p / g (p = 1 when the plan is not phased).
 __device__ __forceinline__ float2 gain_multiplier(double gr, double gi, const double2* phase, size_t i) {
@@ -692,30 +424,6 @@ __device__ __forceinline__ float2 gain_multiplier(double gr, double gi, const do
   return make_float2(static_cast<float>(wr), static_cast<float>(wi));
 }
 
-__global__ void adjoint_finalize_kernel(int n, int n_ant, const double2* __restrict__ dldw,
-                                        const double2* __restrict__ gain, const double2* __restrict__ phase,
-                                        const unsigned char* __restrict__ flags,
-                                        double2* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (flags[i % n_ant]) {
-    out[i] = make_double2(0.0, 0.0);
-    return;
-  }
-  const double2 g = gain[i];
-  // w = p / g: dw/dg = -p / g^2, so 2 dL/dconj(g) = 2 dL/dconj(w) (-conj(p) / conj(g)^2)
-  const double ar = g.x * g.x - g.y * g.y, ai = -2.0 * g.x * g.y;   // conj(g)^2
-  const double den = ar * ar + ai * ai;
-  double qr = -ar / den, qi = ai / den;                             // -1 / conj(g)^2
-  if (phase) {
-    const double2 q = phase[i];                                     // times conj(p)
-    const double xr = qr * q.x + qi * q.y, xi = qi * q.x - qr * q.y;
-    qr = xr;
-    qi = xi;
-  }
-  const double2 d = dldw[i];
-  out[i] = make_double2(2.0 * (d.x * qr - d.y * qi), 2.0 * (d.x * qi + d.y * qr));
-}
 
 // g and w = 1/g from device gains (no host round trip).
 __global__ void set_gains_kernel(int n, const double2* __restrict__ g_in, double2* __restrict__ g,
@@ -950,42 +658,7 @@ void shape_n(ImageKernelShape* o) {
   o->max_ant = Cfg<N>::BT * kMaxAntPerThread;
 }
 
-template <int N>
-cudaError_t adjoint_n(const AdjointArgs& a, cudaStream_t s) {
-  cudaError_t e;
-  if (a.n_ant <= Cfg<N>::BT) {
-    e = cudaFuncSetAttribute(epic_image_adjoint<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(a.smem));
-    if (e != cudaSuccess) return e;
-    epic_image_adjoint<N, 1><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(epic_image_adjoint<N, kMaxAntPerThread>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(a.smem));
-    if (e != cudaSuccess) return e;
-    epic_image_adjoint<N, kMaxAntPerThread><<<a.grid, Cfg<N>::BT, a.smem, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
 }  // namespace
-
-cudaError_t launch_adjoint(int n, const AdjointArgs& a, cudaStream_t s) {
-  switch (n) {
-    case 16: return adjoint_n<16>(a, s);
-    case 32: return adjoint_n<32>(a, s);
-    case 64: return adjoint_n<64>(a, s);
-    case 128: return adjoint_n<128>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_adjoint_finalize(int n_chan, int n_ant, const double2* dldw, const double2* gain,
-                                    const double2* phase, const unsigned char* flags, double2* out,
-                                    cudaStream_t s) {
-  const int n = n_chan * n_ant;
-  adjoint_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, n_ant, dldw, gain, phase, flags, out);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_average_channels(int n_ant, int c_lo, int c_hi, const unsigned char* flags, double2* gain,
                                     float2* wgain, const double2* phase, cudaStream_t s) {
@@ -1063,20 +736,6 @@ int image_rs(int rows_alloc) {
   return rs;
 }
 
-size_t adjoint_smem_bytes(int n, int rows_alloc, int rs, int n_ant) {
-  int groups = 0, zg = 0;
-  switch (n) {
-    case 16: groups = Geo<16>::GROUPS; zg = Geo<16>::ZG; break;
-    case 32: groups = Geo<32>::GROUPS; zg = Geo<32>::ZG; break;
-    case 64: groups = Geo<64>::GROUPS; zg = Geo<64>::ZG; break;
-    case 128: groups = Geo<128>::GROUPS; zg = Geo<128>::ZG; break;
-    default: return 0;
-  }
-  // grid window [rows][N], transposed / row-major spectra [N][rs], exchange, twiddles, E' [Na]
-  const size_t elems = static_cast<size_t>(rows_alloc) * n + static_cast<size_t>(n) * rs +
-                       static_cast<size_t>(groups) * zg + n + n_ant;
-  return elems * sizeof(float2);
-}
 
 int image_rs_fused(int rows_alloc) {
   int rs = ((rows_alloc + 7) / 8) * 8;     // room for the (row ^ (kx & 7)) swizzle

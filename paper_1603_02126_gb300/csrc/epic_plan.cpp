@@ -161,6 +161,7 @@ struct epic_plan_s {
   int tune_row_frames = 2;      // unfused row kernel: frames per step
   int wait_limit = 0;           // warp-specialised form: polls per bounded wait (0 = default)
   int persistent = 0;           // unfused FP32, N = 256 / 512: one persistent launch per call
+  int adjoint_precision = EPIC_PREC_FP32;   // arithmetic of the adjoint's transforms
   DevBuf<unsigned> d_gbar;      // grid barrier {count, generation, abort}
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -1687,6 +1688,14 @@ epic_status epic_plan_set_wait_limit(epic_plan_t p, int polls) {
   return EPIC_OK;
 }
 
+epic_status epic_plan_set_adjoint_precision(epic_plan_t p, int precision) {
+  if (epic_status s = check_plan(p)) return s;
+  if (precision != EPIC_PREC_FP32 && precision != EPIC_PREC_BF16)
+    return fail(EPIC_ERR_INVALID_ARG, "adjoint precision must be EPIC_PREC_FP32 or EPIC_PREC_BF16");
+  p->adjoint_precision = precision;
+  return EPIC_OK;
+}
+
 epic_status epic_plan_sync(epic_plan_t p, int* n_held) {
   if (epic_status s = check_plan(p)) return s;
   EPIC_CUDA(cudaStreamSynchronize(p->stream));
@@ -2020,8 +2029,9 @@ epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_t
   a.gcnt = p->d_ugcnt.p;
   a.gent = p->d_ugent.p;
   a.gbase = p->d_ugbase.p;
-  a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs, p->na);
-  EPIC_CUDA(epic::launch_adjoint(p->n, a, p->stream));
+  const bool bf16 = p->adjoint_precision == EPIC_PREC_BF16;
+  a.smem = epic::adjoint_smem_bytes(p->n, p->rows_alloc, p->rs, p->na, bf16);
+  EPIC_CUDA(epic::launch_adjoint(p->n, a, bf16, p->stream));
   EPIC_CUDA(epic::launch_adjoint_finalize(p->nc, p->na, p->d_dldw.p, p->d_gain.p, p->d_phase.p, p->d_flags.p,
                                           reinterpret_cast<double2*>(d_grad_g), p->stream));
   return EPIC_OK;

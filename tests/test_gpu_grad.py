@@ -76,6 +76,60 @@ def test_adjoint_lwa_ci4_n128_matches_oracle():
     assert err <= 1e-4, err
 
 
+# BF16 transforms: 8-bit significands through ~4 log2(N) butterfly levels;
+# measured 0.9e-3 - 2.6e-3 relative L2 on these cases
+BF16_GRAD_TOL = 1e-2
+
+
+@pytest.mark.parametrize("n,na,diam,T", [(32, 14, 12.0, 47), (64, 40, 26.0, 33), (32, 150, 18.0, 21)])
+def test_adjoint_bf16_matches_oracle(n, na, diam, T):
+    """The BF16 frame-pair adjoint against the FP64 analytic gradient: odd
+    frame counts (the last frame of a unit paired with a zero frame) and
+    Na above the CTA size (several antennas per thread); switching back to
+    FP32 gives the FP32 result."""
+    from paper_1603_02126_gb300 import Plan
+    rng, ant, freqs, g_true, sky, E, fl = _case(n=n, na=na, diam=diam, T=T)
+    g = g_true * (1 + 0.15 * (rng.normal(size=g_true.shape) + 1j * rng.normal(size=g_true.shape)))
+    oplan = O.Plan(ant, freqs, n, 0.5, flags=fl)
+    M = O.model_image(oplan, sky)
+    ref = O.chi2_gradient(oplan, E.astype(np.complex128), g, M)
+    p = Plan(ant, freqs, n, 0.5, input="c64", flags=fl)
+    d, Mt = torch.from_numpy(E).cuda(), torch.from_numpy(M).cuda()
+    p.set_adjoint_precision("bf16")
+    _, grad = _gpu_grad(p, d, g, Mt)
+    err = np.linalg.norm(grad - ref) / np.linalg.norm(ref)
+    cos = np.real(np.vdot(grad, ref)) / (np.linalg.norm(grad) * np.linalg.norm(ref))
+    print(f"bf16 adjoint n={n} na={na} T={T}: rel L2 {err:.3e}, cosine {cos:.6f}")
+    assert err <= BF16_GRAD_TOL, err
+    assert np.all(grad[:, 3] == 0)
+    p.set_adjoint_precision("fp32")
+    _, grad32 = _gpu_grad(p, d, g, Mt)
+    assert np.linalg.norm(grad32 - ref) / np.linalg.norm(ref) <= 1e-4
+    with pytest.raises(ValueError):
+        p.set_adjoint_precision("fp16")
+
+
+def test_adjoint_bf16_lwa_ci4_n128():
+    """The differentiation workload's array and grid (Na = 256, N = 128,
+    4-bit voltages), BF16 transforms."""
+    from paper_1603_02126_gb300 import Plan
+    w = synth.workload("lwa_diff", n_chan=2, n_time=25)
+    E = synth.voltages(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:60], 25, w["noise_power"],
+                       w["rng"])
+    b = synth.quantise_ci4(E, w["lsb"])
+    Eint = O.unpack_ci4(b) * w["lsb"][None, :, None]
+    oplan = O.Plan(w["ant_xy"], w["freqs"], 128, 0.5)
+    M = O.model_image(oplan, w["model"])
+    g = w["gains"] * 1.05
+    ref = O.chi2_gradient(oplan, Eint, g, M)
+    p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, input="ci4", voltage_scale=w["lsb"])
+    p.set_adjoint_precision("bf16")
+    _, grad = _gpu_grad(p, torch.from_numpy(b).cuda(), g, torch.from_numpy(M).cuda())
+    err = np.linalg.norm(grad - ref) / np.linalg.norm(ref)
+    print(f"bf16 adjoint LWA N=128: rel L2 {err:.3e}")
+    assert err <= BF16_GRAD_TOL, err
+
+
 def test_adjoint_gradient_finite_differences_on_gpu():
     """dL = Re(conj(grad) dg) with central differences (step 1e-3) of the
     GPU forward pass itself."""
@@ -139,3 +193,11 @@ def test_adam_solve_vs_epical():
     err_epical = O.gain_error(O.align_phase(pe.gains()[0], g_true[0]), g_true[0])
     err0 = O.gain_error(O.align_phase(g0.cpu().numpy()[0], g_true[0]), g_true[0])
     assert err_adam < 0.6 * err0 and err_epical < 1e-4, (err0, err_adam, err_epical)
+    # the same solve on BF16 gradients
+    p.set_adjoint_precision("bf16")
+    gb = solve_gains(p, d, M, g0, steps=600, lr=0.03, decay=0.992)
+    with torch.no_grad():
+        lb = float(chi2(EpicImageFn.apply(gb, d, p), M))
+    err_b = O.gain_error(O.align_phase(gb.cpu().numpy()[0], g_true[0]), g_true[0])
+    print(f"Adam fp32: loss {l1 / l0:.2e} of start, gain err {err_adam:.3e}; bf16: {lb / l0:.2e}, {err_b:.3e}")
+    assert lb < 1e-2 * l0 and err_b < 0.6 * err0, (l0, lb, err0, err_b)
