@@ -43,7 +43,7 @@ FP32_LANES_PER_SM = 128
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused image launch
 # on this workload, with kernel_sha() of the sources it was taken at;
 # ignored when those sources have changed since.
-TRAFFIC = {"kernel_sha": "992cfe64f2ec", "bytes_per_launch": 183077376}
+TRAFFIC = {"kernel_sha": "ffbd609a2fe4", "bytes_per_launch": 182208512}
 
 
 def kernel_sha() -> str:
@@ -491,7 +491,7 @@ def profile_case(name):
         p.update()
         p.image(d, img)
         p.update()
-    elif name == "grad_lwa":           # differentiation form, 16 channels, 1024 samples
+    elif name in ("grad_lwa", "grad_lwa_bf16"):   # differentiation form, 16 channels, 1024 samples
         from paper_1603_02126_gb300.autograd import EpicImageFn, chi2
         w = synth.workload("lwa_diff", n_time=1024)
         v = synth.voltages_ci4_torch(w["ant_xy"], w["freqs"], w["gains"], w["sky"][:50], w["n_time"],
@@ -501,6 +501,8 @@ def profile_case(name):
         M = pm.image(mf) * mf.shape[0]
         p = Plan(w["ant_xy"], w["freqs"], 128, 0.5, support=3, param=0.5, input="ci4",
                  voltage_scale=w["lsb"])
+        if name == "grad_lwa_bf16":
+            p.set_adjoint_precision("bf16")
         for _ in range(2):
             g = torch.from_numpy(w["gains"]).cuda().requires_grad_(True)
             chi2(EpicImageFn.apply(g, v, p), M).backward()
@@ -603,7 +605,7 @@ def main():
                     help="skip the precision / batching / differentiation forms")
     ap.add_argument("--case", default=None,
                     help="run one untimed profiling workload (fused_lwa, tc_compact, unfused_lwa, "
-                         "grad_lwa, hex_unfused, cluster_compact, multipix_lwa, noise_lwa) and exit")
+                         "grad_lwa, grad_lwa_bf16, hex_unfused, cluster_compact, multipix_lwa, noise_lwa) and exit")
     ap.add_argument("--n-time", type=int, default=None,
                     help="samples per interval (default: the workload's 10000)")
     args = ap.parse_args()

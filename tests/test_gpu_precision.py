@@ -1,6 +1,6 @@
-"""Reduced-precision form on the GPU: the column DFT on tcgen05 tensor cores
-in FP16 and BF16 (FP32 accumulation, per-frame power-of-two scaling), FP32
-gridding and row FFTs, FP64 image accumulation.  Each case states its image
+"""Reduced-precision form on the GPU: the row and column DFTs on tcgen05
+tensor cores in FP16 and BF16 (FP32 accumulation, per-frame power-of-two
+scaling), FP32 gridding, FP64 image accumulation.  Each case states its image
 error against the FP64 oracle; the bar is relative L2 <= 3e-3."""
 import numpy as np
 import pytest
@@ -54,6 +54,34 @@ def test_tensor_core_image_error(prec, n, na, diam, C, T):
     ref, _ = O.image_interval(O.Plan(ant, freqs, n, 0.5), Eint, gcur)
     err = _rel(img, ref)
     print(f"{prec} N={n} image rel-L2 vs FP64 oracle: {err:.3e}")
+    assert err <= LP_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tensor_core_wide_window(prec):
+    """An array elongated in x (about 228 x 120 occupied cells at N = 256):
+    the row DFT's K extent is 2 x 256 window columns (eight 64-element
+    chunks per tile) against 2 x 128 in the square cases."""
+    from paper_1603_02126_gb300 import Plan
+    rng = np.random.default_rng(91)
+    ant = synth.layout_ellipse(300, 290.0, 150.0, rng, 1.0)
+    freqs = np.array([60e6])
+    sky = np.vstack([[0.0, 0.0, 20.0], synth.sky_powerlaw(10, 0.5, 5.0, rng)[1:]])
+    gains = synth.true_gains(1, 300, rng)
+    E = synth.voltages(ant, freqs, gains, sky, 40, sky[:, 2].sum() / 5, rng)
+    lsb = np.full(1, np.sqrt(np.mean(np.abs(E) ** 2) / 2) / 2)
+    b = synth.quantise_ci4(E, lsb)
+    Eint = O.unpack_ci4(b) * lsb[None, :, None]
+    oplan = O.Plan(ant, freqs, 256, 0.5)
+    bx, by = oplan.base[0][:, 0], oplan.base[0][:, 1]
+    cols, rows = bx.max() - bx.min() + 3, by.max() - by.min() + 3
+    assert 2 * cols > 256 and 2 * rows <= 256, (rows, cols)
+    p = Plan(ant, freqs, 256, 0.5, input="ci4", voltage_scale=lsb, precision=prec)
+    img = p.image(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert p.sync() == 0
+    ref, _ = O.image_interval(oplan, Eint, np.ones((1, 300), complex))
+    err = _rel(img, ref)
+    print(f"{prec} wide window ({rows} x {cols} cells) image rel-L2 vs FP64 oracle: {err:.3e}")
     assert err <= LP_TOL
 
 
