@@ -693,15 +693,10 @@ epic_status image_tc(epic_plan_t p, const void* d_volt, long long n_time, double
   return EPIC_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* epic_last_error(void) { return g_last_error.c_str(); }
-
-epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
-  if (!out || !d) return fail(EPIC_ERR_INVALID_ARG, "NULL argument");
-  *out = nullptr;
+// Checks of the plan descriptor; the fused kernel's launch shape for it and
+// which of the fused / unfused forms can take it.
+epic_status validate_desc(const epic_plan_desc* d, epic::ImageKernelShape* shape, bool* fused_shape,
+                          bool* unfused_ok) {
   if (d->n_ant < 1 || d->n_chan < 1) return fail(EPIC_ERR_INVALID_ARG, "n_ant and n_chan must be >= 1");
   if (!d->ant_xy_m || !d->freq_hz) return fail(EPIC_ERR_INVALID_ARG, "ant_xy_m and freq_hz are required");
   if (!is_pow2(d->grid_n) || d->grid_n < 16)
@@ -737,43 +732,26 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       (!epic::cluster_supported(d->grid_n) || d->n_ant > 256 * epic::cluster_size(d->grid_n) ||
        d->precision != EPIC_PREC_FP32))
     return fail(EPIC_ERR_UNSUPPORTED, "cluster path: FP32, grid_n 256 or 512, n_ant <= 256 x cluster size");
-  epic::ImageKernelShape shape{};
-  const bool fused_shape = epic::image_kernel_shape(d->grid_n, &shape) && d->n_ant <= shape.max_ant;
-  const bool unfused_ok = epic::unfused_supported(d->grid_n);
+  *fused_shape = epic::image_kernel_shape(d->grid_n, shape) && d->n_ant <= shape->max_ant;
+  *unfused_ok = epic::unfused_supported(d->grid_n);
   if (d->path == EPIC_PATH_PIPED && !epic::piped_supported(d->grid_n, d->n_ant))
     return fail(EPIC_ERR_UNSUPPORTED, "warp-specialised fused path: grid_n 64 or 128, n_ant <= 512");
-  if ((d->path == EPIC_PATH_FUSED || d->path == EPIC_PATH_PIPED) && !fused_shape)
+  if ((d->path == EPIC_PATH_FUSED || d->path == EPIC_PATH_PIPED) && !*fused_shape)
     return fail(EPIC_ERR_UNSUPPORTED, "fused path: grid_n must be 16..128 and n_ant <= " +
-                                          std::to_string(shape.max_ant > 0 ? shape.max_ant : 2048));
-  if (d->path == EPIC_PATH_UNFUSED && !unfused_ok)
+                                          std::to_string(shape->max_ant > 0 ? shape->max_ant : 2048));
+  if (d->path == EPIC_PATH_UNFUSED && !*unfused_ok)
     return fail(EPIC_ERR_UNSUPPORTED, "unfused path: grid_n must be 32..512");
-  if (!fused_shape && !unfused_ok)
+  if (!*fused_shape && !*unfused_ok)
     return fail(EPIC_ERR_UNSUPPORTED, "grid_n must be 16..512 in this build");
+  return EPIC_OK;
+}
 
-  epic_plan_s* p = new (std::nothrow) epic_plan_s();
-  if (!p) return fail(EPIC_ERR_OOM, "host allocation failed");
-  p->na = d->n_ant;
-  p->nc = d->n_chan;
-  p->n = d->grid_n;
-  p->k = d->kernel_support;
-  p->kernel = d->kernel;
-  p->kparam = d->kernel_param;
-  if (d->kernel_param_ant) p->kparam_ant.assign(d->kernel_param_ant, d->kernel_param_ant + d->n_ant);
-  p->cell = d->cell_wavelengths;
-  p->input = d->input;
-  p->ant.assign(d->ant_xy_m, d->ant_xy_m + 2 * d->n_ant);
-  p->freq.assign(d->freq_hz, d->freq_hz + d->n_chan);
-  p->vscale.assign(d->n_chan, 1.0f);
-  if (d->voltage_scale) p->vscale.assign(d->voltage_scale, d->voltage_scale + d->n_chan);
-  p->flags.assign(d->n_ant, 0);
-  if (d->flags)
-    for (int a = 0; a < d->n_ant; ++a) p->flags[a] = d->flags[a] ? 1 : 0;
-  p->stream = static_cast<cudaStream_t>(d->cuda_stream);
-  p->shape = shape;
-  if (d->workspace_bytes) p->workspace_budget = d->workspace_bytes;
-  p->persistent = d->batch_persistent ? 1 : 0;
-
-  // ---- gridding tables (Eq. 9), FP64 ----
+// Gridding tables of Eq. 9 in FP64 (stencil centres p->base, normalised
+// taps p->w64), every channel's occupied window (y0, rows, x0, cols), and
+// the device forms: cell0 [C][Na] = window row * N + absolute column of
+// the first tap, wts [C][Na][K*K] = taps with the centring sign of Eq. 10
+// and 1/Na folded in.
+epic_status build_grid_tables(epic_plan_s* p, std::vector<int>& cell0, std::vector<float>& wts) {
   const int Na = p->na, C = p->nc, N = p->n, K = p->k, KK = K * K, h = (K - 1) / 2;
   p->base.assign(static_cast<size_t>(C) * Na * 2, 0);
   p->w64.assign(static_cast<size_t>(C) * Na * KK, 0.0);
@@ -781,14 +759,11 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   p->rows.assign(C, 0);
   p->x0.assign(C, 0);
   p->cols.assign(C, 0);
-  std::vector<int> cell0(static_cast<size_t>(C) * Na, -1);
-  std::vector<float> wts(static_cast<size_t>(C) * Na * KK, 0.0f);
+  cell0.assign(static_cast<size_t>(C) * Na, -1);
+  wts.assign(static_cast<size_t>(C) * Na * KK, 0.0f);
   int n_unflagged = 0;
   for (int a = 0; a < Na; ++a) n_unflagged += p->flags[a] ? 0 : 1;
-  if (n_unflagged == 0) {
-    delete p;
-    return fail(EPIC_ERR_INVALID_ARG, "every antenna is flagged");
-  }
+  if (n_unflagged == 0) return fail(EPIC_ERR_INVALID_ARG, "every antenna is flagged");
   for (int c = 0; c < C; ++c) {
     const double f = p->freq[c];
     int ymin = N, ymax = -1;
@@ -801,7 +776,6 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
       if (!(std::fabs(bxd) < 1e9 && std::fabs(byd) < 1e9)) {
         if (p->flags[a]) continue;
-        delete p;
         return fail(EPIC_ERR_GRID_TOO_SMALL, "antenna far outside the grid");
       }
       const int bx = static_cast<int>(bxd), by = static_cast<int>(byd);
@@ -809,7 +783,6 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       p->base[ob + 1] = by;
       if (p->flags[a]) continue;
       if (bx - h < 0 || bx + h >= N || by - h < 0 || by + h >= N) {
-        delete p;
         char msg[160];
         std::snprintf(msg, sizeof msg, "antenna %d channel %d: stencil outside the %dx%d grid", a, c, N, N);
         return fail(EPIC_ERR_GRID_TOO_SMALL, msg);
@@ -832,10 +805,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
           w[dy * K + dx] = v;
           sum += v;
         }
-      if (!(sum > 0)) {
-        delete p;
+      if (!(sum > 0))
         return fail(EPIC_ERR_INVALID_ARG, "gridding kernel has no support for antenna " + std::to_string(a));
-      }
       for (int i = 0; i < KK; ++i) w[i] /= sum;
       ymin = std::min(ymin, by - h);
       ymax = std::max(ymax, by + h);
@@ -868,14 +839,19 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
   }
 
-  // ---- launch shape ----
+  return EPIC_OK;
+}
+
+// Launch shape and path of the plan: the tensor-core form's K extent for
+// FP16/BF16, else the fused kernel's frames per step and gather-table
+// placement (or the warp-specialised form), the cluster form when asked
+// for, else the plain unfused path; CTAs per launch.
+epic_status choose_path(epic_plan_s* p, const epic_plan_desc* d, bool fused_shape, bool unfused_ok) {
+  const int Na = p->na, N = p->n, KK = p->k * p->k;
   p->rs = epic::image_rs(p->rows_alloc);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaGetDevice");
-  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   p->device = dev;
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -883,17 +859,12 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
   bool fused = fused_shape && d->path != EPIC_PATH_UNFUSED && d->precision == EPIC_PREC_FP32;
   p->precision = d->precision;
   if (p->precision != EPIC_PREC_FP32) {
-    if (!epic::tc_supported(N, p->rows_alloc)) {
-      delete p;
+    if (!epic::tc_supported(N, p->rows_alloc))
       return fail(EPIC_ERR_UNSUPPORTED, "FP16/BF16 form: grid_n must be 128 or 256 and the array "
                                         "footprint at most 128 grid rows");
-    }
     p->kp = epic::tc_kp(p->rows_alloc);
     e = epic::tc_prepare(p->precision == EPIC_PREC_BF16, epic::tc_smem(p->kp));
-    if (e != cudaSuccess) {
-      delete p;
-      return cuda_fail(e, "tensor-core kernel attributes");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel attributes");
   }
   p->rs_fused = epic::image_rs_fused(p->rows_alloc);
   if (fused && d->path == EPIC_PATH_PIPED && epic::piped_supported(N, Na)) {
@@ -912,10 +883,8 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       p->gsmem = 0;
     }
   }
-  if (d->path == EPIC_PATH_PIPED && !p->piped) {
-    delete p;
+  if (d->path == EPIC_PATH_PIPED && !p->piped)
     return fail(EPIC_ERR_UNSUPPORTED, "warp-specialised fused path: array footprint exceeds shared memory");
-  }
   if (fused && !p->piped) {
     // shape preference: two frames per step, then one; the gather table in
     // shared memory when it fits (entries per channel <= Na K^2 taps), else
@@ -939,10 +908,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
                               std::to_string(epic::image_smem_bytes(N, Na, p->rs_fused, 1)) +
                               " B of shared memory in the fused kernel (limit " +
                               std::to_string(smem_optin) + ")";
-      if (d->path == EPIC_PATH_FUSED || !unfused_ok) {
-        delete p;
-        return fail(EPIC_ERR_UNSUPPORTED, msg);
-      }
+      if (d->path == EPIC_PATH_FUSED || !unfused_ok) return fail(EPIC_ERR_UNSUPPORTED, msg);
       fused = false;
     }
   }
@@ -965,7 +931,6 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       p->ctas = ncl * p->cs;
       p->path = EPIC_PATH_CLUSTER;
     } else if (d->path == EPIC_PATH_CLUSTER) {
-      delete p;
       return e != cudaSuccess && e != cudaErrorInvalidValue ? cuda_fail(e, "cluster kernel attributes")
                                                             : fail(EPIC_ERR_UNSUPPORTED, "cluster kernel cannot be resident");
     } else {
@@ -979,11 +944,9 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     int per_sm = 0;
     e = p->piped ? epic::piped_prepare(N, p->smem, p->gsmem != 0, &per_sm)
                  : epic::image_kernel_prepare(N, p->smem, Na, p->steps, &per_sm);
-    if (e != cudaSuccess || per_sm < 1) {
-      delete p;
+    if (e != cudaSuccess || per_sm < 1)
       return e != cudaSuccess ? cuda_fail(e, "image kernel attributes")
                               : fail(EPIC_ERR_UNSUPPORTED, "image kernel cannot be resident");
-    }
     p->ctas = per_sm * p->sms;
     p->path = EPIC_PATH_FUSED;
   } else {
@@ -991,6 +954,96 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     p->ctas = p->sms;
     p->path = EPIC_PATH_UNFUSED;
   }
+
+  return EPIC_OK;
+}
+
+// Cluster-path tables: each antenna's stencil (top row << 16 | first
+// column) in window coordinates, the antennas of every channel sorted by
+// top row, and per CTA of a cluster the sorted range whose stencil rows
+// meet the CTA's row block (rows per CTA = ceil(rows / cluster size)).
+void build_cluster_tables(const epic_plan_s* p, std::vector<int>& rowcol, std::vector<int>& order,
+                          std::vector<int2>& ranges) {
+  const int Na = p->na, C = p->nc, K = p->k, h = (K - 1) / 2;
+  const int CS = p->cs;
+  rowcol.assign(static_cast<size_t>(C) * Na, -1);
+  order.assign(static_cast<size_t>(C) * Na, 0);
+  ranges.assign(static_cast<size_t>(C) * CS, make_int2(0, 0));
+  for (int c = 0; c < C; ++c) {
+    std::vector<std::pair<int, int>> tops;
+    for (int a = 0; a < Na; ++a) {
+      if (p->flags[a]) continue;
+      const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
+      const int top = p->base[ob + 1] - h - p->y0[c];
+      const int col = p->base[ob] - h - p->x0[c];
+      rowcol[static_cast<size_t>(c) * Na + a] = (top << 16) | col;
+      tops.emplace_back(top, a);
+    }
+    std::stable_sort(tops.begin(), tops.end());
+    for (size_t i = 0; i < tops.size(); ++i) order[static_cast<size_t>(c) * Na + i] = tops[i].second;
+    const int rpc = (p->rows[c] + CS - 1) / CS;
+    for (int q = 0; q < CS; ++q) {
+      const int lo_top = q * rpc - K + 1, hi_top = (q + 1) * rpc - 1;
+      int lo = 0, hi = 0;
+      while (lo < static_cast<int>(tops.size()) && tops[lo].first < lo_top) ++lo;
+      hi = lo;
+      while (hi < static_cast<int>(tops.size()) && tops[hi].first <= hi_top) ++hi;
+      ranges[static_cast<size_t>(c) * CS + q] = make_int2(lo, hi);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* epic_last_error(void) { return g_last_error.c_str(); }
+
+epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
+  if (!out || !d) return fail(EPIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  epic::ImageKernelShape shape{};
+  bool fused_shape = false, unfused_ok = false;
+  if (epic_status st = validate_desc(d, &shape, &fused_shape, &unfused_ok)) return st;
+
+  epic_plan_s* p = new (std::nothrow) epic_plan_s();
+  if (!p) return fail(EPIC_ERR_OOM, "host allocation failed");
+  p->na = d->n_ant;
+  p->nc = d->n_chan;
+  p->n = d->grid_n;
+  p->k = d->kernel_support;
+  p->kernel = d->kernel;
+  p->kparam = d->kernel_param;
+  if (d->kernel_param_ant) p->kparam_ant.assign(d->kernel_param_ant, d->kernel_param_ant + d->n_ant);
+  p->cell = d->cell_wavelengths;
+  p->input = d->input;
+  p->ant.assign(d->ant_xy_m, d->ant_xy_m + 2 * d->n_ant);
+  p->freq.assign(d->freq_hz, d->freq_hz + d->n_chan);
+  p->vscale.assign(d->n_chan, 1.0f);
+  if (d->voltage_scale) p->vscale.assign(d->voltage_scale, d->voltage_scale + d->n_chan);
+  p->flags.assign(d->n_ant, 0);
+  if (d->flags)
+    for (int a = 0; a < d->n_ant; ++a) p->flags[a] = d->flags[a] ? 1 : 0;
+  p->stream = static_cast<cudaStream_t>(d->cuda_stream);
+  p->shape = shape;
+  if (d->workspace_bytes) p->workspace_budget = d->workspace_bytes;
+  p->persistent = d->batch_persistent ? 1 : 0;
+
+  // ---- gridding tables (Eq. 9), FP64 ----
+  std::vector<int> cell0;
+  std::vector<float> wts;
+  if (epic_status st = build_grid_tables(p, cell0, wts)) {
+    delete p;
+    return st;
+  }
+  const int Na = p->na, C = p->nc, N = p->n, K = p->k, h = (K - 1) / 2;
+
+  // ---- launch shape ----
+  if (epic_status st = choose_path(p, d, fused_shape, unfused_ok)) {
+    delete p;
+    return st;
+  }
+  const bool fused = p->path == EPIC_PATH_FUSED;
 
   // ---- device tables ----
   std::vector<float2> twid(N);
@@ -1032,39 +1085,9 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
     }
   }
   std::vector<float2> pixph(C, make_float2(1.0f, 0.0f));
-  // cluster path: stencil (top row, first column) in window coordinates,
-  // antennas sorted by top row, and per CTA the sorted range whose stencil
-  // rows meet the CTA's row block (rows per CTA = ceil(rows / CS))
   std::vector<int> rowcol, order;
   std::vector<int2> ranges;
-  if (p->path == EPIC_PATH_CLUSTER) {
-    const int CS = p->cs;
-    rowcol.assign(static_cast<size_t>(C) * Na, -1);
-    order.assign(static_cast<size_t>(C) * Na, 0);
-    ranges.assign(static_cast<size_t>(C) * CS, make_int2(0, 0));
-    for (int c = 0; c < C; ++c) {
-      std::vector<std::pair<int, int>> tops;
-      for (int a = 0; a < Na; ++a) {
-        if (p->flags[a]) continue;
-        const size_t ob = (static_cast<size_t>(c) * Na + a) * 2;
-        const int top = p->base[ob + 1] - h - p->y0[c];
-        const int col = p->base[ob] - h - p->x0[c];
-        rowcol[static_cast<size_t>(c) * Na + a] = (top << 16) | col;
-        tops.emplace_back(top, a);
-      }
-      std::stable_sort(tops.begin(), tops.end());
-      for (size_t i = 0; i < tops.size(); ++i) order[static_cast<size_t>(c) * Na + i] = tops[i].second;
-      const int rpc = (p->rows[c] + CS - 1) / CS;
-      for (int q = 0; q < CS; ++q) {
-        const int lo_top = q * rpc - K + 1, hi_top = (q + 1) * rpc - 1;
-        int lo = 0, hi = 0;
-        while (lo < static_cast<int>(tops.size()) && tops[lo].first < lo_top) ++lo;
-        hi = lo;
-        while (hi < static_cast<int>(tops.size()) && tops[hi].first <= hi_top) ++hi;
-        ranges[static_cast<size_t>(c) * CS + q] = make_int2(lo, hi);
-      }
-    }
-  }
+  if (p->path == EPIC_PATH_CLUSTER) build_cluster_tables(p, rowcol, order, ranges);
   std::vector<double2> gain(static_cast<size_t>(C) * Na, make_double2(1.0, 0.0));
   std::vector<float2> wgain(static_cast<size_t>(C) * Na, make_float2(1.0f, 0.0f));
 
@@ -1087,7 +1110,7 @@ epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
       return x == cudaErrorMemoryAllocation ? fail(EPIC_ERR_OOM, "device allocation failed")
                                             : cuda_fail(x, "table upload");
     }
-  e = p->d_held.alloc(1);
+  cudaError_t e = p->d_held.alloc(1);
   if (e == cudaSuccess) e = cudaMemset(p->d_held.p, 0, sizeof(int));
   if (e == cudaSuccess) e = p->d_gbar.alloc(4);
   if (e == cudaSuccess) e = cudaMemset(p->d_gbar.p, 0, 4 * sizeof(unsigned));
