@@ -21,14 +21,15 @@
 //                (FP64 atomics).  |E|^2 does not depend on where the window
 //                starts, so both DFTs use window coordinates.
 // tc_cols is a persistent, warp-specialised kernel: warp 0 issues TMA loads
-// (128B-swizzled, 2-stage ring of data tiles; the CTA's DFT tile is loaded
-// once), warp 1 owns the TMEM allocation and issues tcgen05.mma from one
-// thread (M = 128 DFT rows, N = 128 frames, K = 16 per instruction), warps
-// 2-9 drain the double-buffered TMEM accumulators (two warps per lane
-// quarter, 64 frames each).  tc_rows and the X-engine stream both operands
-// through a 4-stage ring (warps 0, 1, and 2-5 for the epilogue).  Every
-// mbarrier wait is bounded; on timeout the kernel records an error flag and
-// winds down.
+// (128B-swizzled; the CTA's DFT tile is loaded once, the data tiles stream
+// through a 4-stage ring of 64-element K chunks, the next tile is
+// prefetched into L2), warp 1 owns the TMEM allocation and issues
+// tcgen05.mma from one thread (M = 128 DFT rows, N = 256 = 128 frames of
+// two columns kx, kx + 1, K = 16 per instruction), warps 2-9 drain the
+// double-buffered TMEM accumulators (one warp per column and lane quarter).  tc_rows and the X-engine stream both
+// operands through a 4-stage ring (warps 0, 1, and 2-5 for the epilogue).
+// Every mbarrier wait is bounded; on timeout the kernel records an error
+// flag, waits (bounded) for its copies and MMAs in flight and winds down.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -233,6 +234,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// Bring one 3-D box into L2 ahead of its load (no shared memory, no barrier).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* tm, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+               ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z,
                                             uint32_t bar) {
   asm volatile(
@@ -291,17 +299,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 constexpr int kTcThreads = 320;          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
-constexpr int kEpiWarps = 8;             // two per TMEM lane quarter, each half the frames
-constexpr int kTile = 128;               // DFT rows and frames per tile
+constexpr int kEpiWarps = 8;             // one per (column half, TMEM lane quarter)
+constexpr int kTile = 128;               // DFT rows, and frames per column half
 constexpr int kChunkBytes = kTile * 128; // one 64-element K chunk of a 128-row tile
-constexpr uint32_t kTmemCols = 256;      // two 128-column accumulators
+constexpr int kColN = 256;               // MMA N of tc_cols: 128 frames of kx, then of kx + 1
+constexpr int kColChunkBytes = kColN * 128;
+constexpr int kColStages = 4;            // K-chunk ring of the data operand
+constexpr uint32_t kTmemCols = 256;      // tc_rows / X-engine: two 128-column accumulators
+constexpr uint32_t kColTmemCols = 512;   // tc_cols: two 256-column accumulators
 
-// Dynamic shared memory of tc_cols_kernel for a K extent of kp elements.
+// Dynamic shared memory of tc_cols_kernel for a K extent of kp elements:
+// the CTA's resident DFT tile and the data ring.
 size_t tc_smem_bytes(int kp) {
   const size_t tile = static_cast<size_t>(kp / 64) * kChunkBytes;
-  return 1024 /*alignment slack*/ + 3 * tile + 256 /*barriers*/;
+  return 1024 /*alignment slack*/ + tile + kColStages * kColChunkBytes + 256 /*barriers*/;
 }
 
+// Column DFT GEMM.  A CTA owns one 128-row DFT tile (rows 2 ky + re/im),
+// resident in shared memory, and walks the data tiles (channel, column
+// pair kx and kx + 1, 128 frames): each MMA is M = 128 DFT rows by N = 256
+// (the 128 frames of kx, then those of kx + 1; one 3-D TMA box of two
+// columns) by K = 16, the shape that keeps the tensor pipe busiest for one
+// CTA.  Data chunks stream through a 4-stage ring of 64-element K chunks;
+// two 256-column TMEM accumulators alternate between the MMA and the
+// epilogue.
 template <bool kBf16>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_cols_kernel(const __grid_constant__ CUtensorMap tm_dft, const __grid_constant__ CUtensorMap tm_data,
@@ -311,35 +332,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int kc_n = A.kp / 64;
   const uint32_t tile_bytes = static_cast<uint32_t>(kc_n) * kChunkBytes;
-  unsigned char* sA = base;                         // DFT tile (resident)
-  unsigned char* sD = base + tile_bytes;            // 2 data stages
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 3 * tile_bytes);
-  // bars: 0,1 full; 2,3 empty; 4,5 tmem_full; 6,7 tmem_empty; 8 dft_full
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+  unsigned char* sA = base;                         // the DFT tile (resident)
+  unsigned char* sD = base + tile_bytes;            // data ring, kColStages chunks
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sD + kColStages * kColChunkBytes);
+  // bars: [0, S) full; [S, 2S) empty; 2S + {0,1} tmem_full; 2S + {2,3}
+  // tmem_empty; 2S + 4 dft_full; 2S + 5 drain
+  constexpr int S = kColStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * S + 7);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int C = A.u.n_chan, N = A.u.grid_n;
-  const int MB = 2 * N / kTile;
+  const int MB = 2 * N / kTile;                     // DFT tiles
   const int tbk = (nt + kTile - 1) / kTile;
-  const long long tiles = static_cast<long long>(MB) * C * N * tbk;
-  const int G = gridDim.x;                          // multiple of MB
+  const long long dtiles = static_cast<long long>(C) * (N / 2) * tbk;
+  const int G = gridDim.x / MB;                     // CTAs per DFT tile (grid is a multiple of MB)
   const int mb = blockIdx.x % MB;
+  const long long u0 = blockIdx.x / MB;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(bars + i), 1);
-      mbar_init(smem_u32(bars + 2 + i), 1);
-      mbar_init(smem_u32(bars + 4 + i), 1);
-      mbar_init(smem_u32(bars + 6 + i), kEpiWarps);
+      mbar_init(smem_u32(bars + S + i), 1);
     }
-    mbar_init(smem_u32(bars + 8), 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(bars + 2 * S + i), 1);
+      mbar_init(smem_u32(bars + 2 * S + 2 + i), kEpiWarps);
+    }
+    mbar_init(smem_u32(bars + 2 * S + 4), 1);
+    mbar_init(smem_u32(bars + 2 * S + 5), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(kColTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -353,76 +380,110 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_dft)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_data)) : "memory");
-      const uint32_t bdft = smem_u32(bars + 8);
+      const uint32_t bdft = smem_u32(bars + 2 * S + 4);
       mbar_expect_tx(bdft, tile_bytes);
       for (int kc = 0; kc < kc_n; ++kc)
         tma_load_2d(smem_u32(sA + kc * kChunkBytes), &tm_dft, kc * 64, mb * kTile, bdft);
-      int i = 0;
-      for (long long u = blockIdx.x; u < tiles; u += G, ++i) {
-        const int s = i & 1;
-        const uint32_t ph = (i >> 1) & 1;
-        if (!mbar_wait(smem_u32(bars + 2 + s), ph ^ 1, abort_flag, A.err)) break;
-        const long long rest = u / MB;
-        const int tb = static_cast<int>(rest % tbk);
-        const long long ck = rest / tbk;             // c * N + kx
-        const uint32_t bfull = smem_u32(bars + s);
-        mbar_expect_tx(bfull, tile_bytes);
-        for (int kc = 0; kc < kc_n; ++kc)
-          tma_load_3d(smem_u32(sD + s * tile_bytes + kc * kChunkBytes), &tm_data, kc * 64, tb * kTile,
-                      static_cast<int>(ck), bfull);
+      long long it = 0;
+      bool ok = true;
+      for (long long u = u0; ok && u < dtiles; u += G) {
+        const int tb = static_cast<int>(u % tbk);
+        const int ck = static_cast<int>(u / tbk) * 2;   // c * N + kx, kx even
+        // the next data tile into L2 now (first DFT tile's CTA), so that its
+        // chunk loads find it there rather than in DRAM
+        if (mb == 0 && u + G < dtiles) {
+          const long long un = u + G;
+          for (int kc = 0; kc < kc_n; ++kc)
+            tma_prefetch_3d(&tm_data, kc * 64, static_cast<int>(un % tbk) * kTile, static_cast<int>(un / tbk) * 2);
+        }
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % S);
+          const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+          if (!mbar_wait(smem_u32(bars + S + s), ph ^ 1, abort_flag, A.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bfull = smem_u32(bars + s);
+          mbar_expect_tx(bfull, kColChunkBytes);
+          tma_load_3d(smem_u32(sD + s * kColChunkBytes), &tm_data, kc * 64, tb * kTile, ck, bfull);
+        }
+      }
+      if (*abort_flag) {
+        // let the copies still in flight land before the CTA exits (bounded)
+        for (int w = 0; w < (1 << 22) && !mbar_try(smem_u32(bars + 2 * S + 4), 0); ++w) {
+        }
+        for (long long j = it > S ? it - S : 0; j < it; ++j) {
+          const uint32_t bar = smem_u32(bars + j % S), ph = static_cast<uint32_t>((j / S) & 1);
+          for (int w = 0; w < (1 << 22) && !mbar_try(bar, ph); ++w) {
+          }
+        }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | ((kBf16 ? 1u : 0u) << 7) | ((kBf16 ? 1u : 0u) << 10) |
-                             (static_cast<uint32_t>(kTile >> 3) << 17) |
+                             (static_cast<uint32_t>(kColN >> 3) << 17) |
                              (static_cast<uint32_t>(kTile >> 4) << 24);
-      bool ok = mbar_wait(smem_u32(bars + 8), 0, abort_flag, A.err);
+      bool ok = mbar_wait(smem_u32(bars + 2 * S + 4), 0, abort_flag, A.err);
+      tc_fence_after();
+      long long it = 0;
       int i = 0;
-      for (long long u = blockIdx.x; ok && u < tiles; u += G, ++i) {
-        const int s = i & 1, acc = i & 1;
-        const uint32_t ph = (i >> 1) & 1;
-        if (!mbar_wait(smem_u32(bars + 6 + acc), ph ^ 1, abort_flag, A.err)) break;
+      for (long long u = u0; ok && u < dtiles; u += G, ++i) {
+        const int acc = i & 1;
+        const uint32_t aph = static_cast<uint32_t>((i >> 1) & 1);
+        if (!mbar_wait(smem_u32(bars + 2 * S + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
         tc_fence_after();
-        if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sD + s * tile_bytes);
-        for (int kc = 0; kc < kc_n; ++kc)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t off = kc * kChunkBytes + k * 32;
-            mma_f16(d_tmem, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, (kc | k) != 0);
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kColN);
+        for (int kc = 0; kc < kc_n; ++kc, ++it) {
+          const int s = static_cast<int>(it % S);
+          const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+          if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) {
+            ok = false;
+            break;
           }
-        mma_commit(smem_u32(bars + 2 + s));   // data stage free once these MMAs finish
-        mma_commit(smem_u32(bars + 4 + acc)); // accumulator ready
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + kc * kChunkBytes), b0 = smem_u32(sD + s * kColChunkBytes);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(d_tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc, (kc | k) != 0);
+          mma_commit(smem_u32(bars + S + s));   // data chunk free once these MMAs finish
+        }
+        if (ok) mma_commit(smem_u32(bars + 2 * S + acc));   // accumulator ready
+      }
+      if (*abort_flag) {
+        // wait (bounded) for the MMAs already issued before TMEM is freed
+        const uint32_t drain = smem_u32(bars + 2 * S + 5);
+        mma_commit(drain);
+        for (int w = 0; w < (1 << 22) && !mbar_try(drain, 0); ++w) {
+        }
       }
     }
   } else {
     // ---------------- epilogue (warps 2-9) ----------------
     const int q = warp & 3;                        // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;              // which 64 frames of the tile
+    const int half = (warp - 2) >> 2;              // column kx (0) or kx + 1 (1)
     const int r = mb * kTile + q * 32 + lane;      // DFT row = 2 ky + (re, im)
     const int ky = r >> 1;
     int i = 0;
-    for (long long u = blockIdx.x; u < tiles; u += G, ++i) {
+    for (long long u = u0; u < dtiles; u += G, ++i) {
       const int acc = i & 1;
-      const uint32_t ph = (i >> 1) & 1;
-      if (!mbar_wait(smem_u32(bars + 4 + acc), ph, abort_flag, A.err)) break;
+      const uint32_t ph = static_cast<uint32_t>((i >> 1) & 1);
+      if (!mbar_wait(smem_u32(bars + 2 * S + acc), ph, abort_flag, A.err)) break;
       tc_fence_after();
-      const long long rest = u / MB;
-      const int tb = static_cast<int>(rest % tbk);
-      const long long ck = rest / tbk;
-      const int c = static_cast<int>(ck / N), kx = static_cast<int>(ck % N);
+      const int tb = static_cast<int>(u % tbk);
+      const int ck = static_cast<int>(u / tbk) * 2 + half;
+      const int c = ck / N, kx = ck % N;
       float sum = 0.f;
 #pragma unroll
-      for (int ch = 0; ch < kTile / 64; ++ch) {
-        const int col = half * 64 + ch * 32;
+      for (int ch = 0; ch < kTile / 32; ++ch) {
+        const int col = ch * 32;
         const int t = tb * kTile + col + lane;
         const float my_w = (t < nt) ? __ldg(A.finv2 + static_cast<size_t>(t) * C + c) : 0.f;
         float v[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + col), v);
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                      static_cast<uint32_t>(acc * kColN + half * kTile + col),
+                  v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float w = __shfl_sync(fft::kFull, my_w, j);
@@ -431,7 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(bars + 6 + acc));
+      if (lane == 0) mbar_arrive(smem_u32(bars + 2 * S + 2 + acc));
       const float other = __shfl_xor_sync(fft::kFull, sum, 1);
       if ((lane & 1) == 0)
         atomicAdd(A.u.image + (static_cast<size_t>(c) * N + ky) * N + kx,
@@ -442,7 +503,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kColTmemCols)
                  : "memory");
   }
 }
@@ -909,7 +970,7 @@ cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int MB = 2 * a.u.grid_n / kTile;
+  const int MB = 2 * a.u.grid_n / kTile;           // 128-row DFT tiles
   const int grid = (sms / MB) * MB;
   const size_t smem = tc_smem_bytes(a.kp);
   const CUtensorMap* td = static_cast<const CUtensorMap*>(tm_dft);
@@ -989,7 +1050,7 @@ bool tc_make_maps(void* dft, void* hh, int n, int n_chan, int tb_cap, int kp, bo
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(tb_cap),
                           static_cast<cuuint64_t>(n_chan) * n};
     cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * 2, static_cast<cuuint64_t>(kp) * 2 * tb_cap};
-    cuuint32_t box[3] = {64, static_cast<cuuint32_t>(kTile), 1};
+    cuuint32_t box[3] = {64, static_cast<cuuint32_t>(kTile), 2};   // columns kx, kx + 1
     cuuint32_t es[3] = {1, 1, 1};
     if (encode(static_cast<CUtensorMap*>(tm_data), dt, 3, hh, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
