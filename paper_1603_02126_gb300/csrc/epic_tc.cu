@@ -26,8 +26,10 @@
 // prefetched into L2), warp 1 owns the TMEM allocation and issues
 // tcgen05.mma from one thread (M = 128 DFT rows, N = 256 = 128 frames of
 // two columns kx, kx + 1, K = 16 per instruction), warps 2-9 drain the
-// double-buffered TMEM accumulators (one warp per column and lane quarter).  tc_rows and the X-engine stream both
-// operands through a 4-stage ring (warps 0, 1, and 2-5 for the epilogue).
+// double-buffered TMEM accumulators (one warp per column and lane
+// quarter).  tc_rows (N = 256 outputs per MMA, epilogue warps 2-9) and the
+// X-engine (epilogue warps 2-5) stream both operands through a 4-stage
+// ring.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, waits (bounded) for its copies and MMAs in flight and winds down.
 #include <cuda.h>
@@ -733,46 +735,56 @@ __global__ void __launch_bounds__(kXeThreads, 1)
 // Row DFT of the precision form on the tensor cores: H = Gh F_r^T, rows =
 // (frame, window row), K = 2 x window columns (re/im interleaved), outputs
 // (kx, re/im) with F_r the real-expanded DFT over window columns.  Tile =
-// (128 rows, 128 outputs); warp 0 streams 64-element K chunks of both
-// operands through the mbarrier ring, warp 1 issues the MMAs, warps 2-5
-// write each lane's (re, im) pairs of its frame and window row straight into
-// the column GEMM's K-major operand Hh[c][kx][t][2 jw + re/im], skipping
-// rows past the channel's occupied rows (they stay zero).
+// (128 rows, 256 outputs): each MMA is M = 128 by N = 256 by K = 16.  Warp 0
+// streams 64-element K chunks of both operands through a 4-stage mbarrier
+// ring, warp 1 issues the MMAs into two 256-column TMEM accumulators, warps
+// 2-9 (one per output half and lane quarter) write each lane's (re, im)
+// pairs of its frame and window row straight into the column GEMM's K-major
+// operand Hh[c][kx][t][2 jw + re/im], skipping rows past the channel's
+// occupied rows (they stay zero).
+constexpr int kRowN = 256;                       // outputs per tile
+constexpr int kRowStages = 4;
+constexpr uint32_t kRowStageBytes = kChunkBytes + kRowN * 128;   // A chunk + B chunk
+size_t tc_rows_smem_bytes() { return 1024 + kRowStages * kRowStageBytes + 256; }
+
 template <bool kBf16>
-__global__ void __launch_bounds__(kXeThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     tc_rows_kernel(const __grid_constant__ CUtensorMap tm_gh, const __grid_constant__ CUtensorMap tm_fr,
                    const TcArgs A, int nt) {
   using T = typename std::conditional<kBf16, __nv_bfloat16, __half>::type;
   extern __shared__ __align__(1024) unsigned char tr_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tr_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kXeStages * kXeStageBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kXeStages + 5);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kXeStages + 6);
+  constexpr int S = kRowStages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * kRowStageBytes);
+  // bars: [0, S) full; [S, 2S) empty; 2S + {0,1} tmem_full; 2S + {2,3}
+  // tmem_empty; 2S + 4 drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * S + 6);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int C = A.u.n_chan, N = A.u.grid_n;
   const long long rows = static_cast<long long>(nt) * C * A.r_alloc;
   const long long mt_n = (rows + kTile - 1) / kTile;
-  const int nt2 = 2 * N / kTile;
+  const int nt2 = 2 * N / kRowN;
   const long long tiles = mt_n * nt2;
   const int kc_n = A.kr / 64;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kXeStages; ++i) {
+    for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(bars + i), 1);
-      mbar_init(smem_u32(bars + kXeStages + i), 1);
+      mbar_init(smem_u32(bars + S + i), 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(bars + 2 * kXeStages + i), 1);
-      mbar_init(smem_u32(bars + 2 * kXeStages + 2 + i), 4);
+      mbar_init(smem_u32(bars + 2 * S + i), 1);
+      mbar_init(smem_u32(bars + 2 * S + 2 + i), kEpiWarps);
     }
-    mbar_init(smem_u32(bars + 2 * kXeStages + 4), 1);
+    mbar_init(smem_u32(bars + 2 * S + 4), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(kColTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -786,22 +798,27 @@ __global__ void __launch_bounds__(kXeThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_gh)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_fr)) : "memory");
       long long it = 0;
-      for (long long u = blockIdx.x; u < tiles && !*abort_flag; u += gridDim.x) {
+      bool ok = true;
+      for (long long u = blockIdx.x; ok && u < tiles; u += gridDim.x) {
         const int mt = static_cast<int>(u / nt2), ot = static_cast<int>(u % nt2);
         for (int kc = 0; kc < kc_n; ++kc, ++it) {
-          const int s = static_cast<int>(it % kXeStages);
-          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
-          if (!mbar_wait(smem_u32(bars + kXeStages + s), ph ^ 1, abort_flag, A.err)) break;
+          const int s = static_cast<int>(it % S);
+          const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+          if (!mbar_wait(smem_u32(bars + S + s), ph ^ 1, abort_flag, A.err)) {
+            ok = false;
+            break;
+          }
           const uint32_t bfull = smem_u32(bars + s);
-          mbar_expect_tx(bfull, kXeStageBytes);
-          unsigned char* st = base + s * kXeStageBytes;
+          mbar_expect_tx(bfull, kRowStageBytes);
+          unsigned char* st = base + s * kRowStageBytes;
           tma_load_2d(smem_u32(st), &tm_gh, kc * 64, mt * kTile, bfull);
-          tma_load_2d(smem_u32(st + kChunkBytes), &tm_fr, kc * 64, ot * kTile, bfull);
+          tma_load_2d(smem_u32(st + kChunkBytes), &tm_fr, kc * 64, ot * kRowN, bfull);
         }
       }
       if (*abort_flag) {
-        for (long long j = it > kXeStages ? it - kXeStages : 0; j < it; ++j) {
-          const uint32_t bar = smem_u32(bars + j % kXeStages), ph = static_cast<uint32_t>((j / kXeStages) & 1);
+        // let the copies still in flight land before the CTA exits (bounded)
+        for (long long j = it > S ? it - S : 0; j < it; ++j) {
+          const uint32_t bar = smem_u32(bars + j % S), ph = static_cast<uint32_t>((j / S) & 1);
           for (int w = 0; w < (1 << 22) && !mbar_try(bar, ph); ++w) {
           }
         }
@@ -810,47 +827,49 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | ((kBf16 ? 1u : 0u) << 7) | ((kBf16 ? 1u : 0u) << 10) |
-                             (static_cast<uint32_t>(kTile >> 3) << 17) | (static_cast<uint32_t>(kTile >> 4) << 24);
+                             (static_cast<uint32_t>(kRowN >> 3) << 17) | (static_cast<uint32_t>(kTile >> 4) << 24);
       long long it = 0;
       int i = 0;
       bool ok = true;
       for (long long u = blockIdx.x; ok && u < tiles; u += gridDim.x, ++i) {
         const int acc = i & 1;
         const uint32_t aph = (i >> 1) & 1;
-        if (!mbar_wait(smem_u32(bars + 2 * kXeStages + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
+        if (!mbar_wait(smem_u32(bars + 2 * S + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kRowN);
         for (int kc = 0; kc < kc_n; ++kc, ++it) {
-          const int s = static_cast<int>(it % kXeStages);
-          const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
+          const int s = static_cast<int>(it % S);
+          const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
           if (!mbar_wait(smem_u32(bars + s), ph, abort_flag, A.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(base + s * kXeStageBytes), b0 = a0 + kChunkBytes;
+          const uint32_t a0 = smem_u32(base + s * kRowStageBytes), b0 = a0 + kChunkBytes;
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             mma_f16(d_tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc, (kc | k) != 0);
-          mma_commit(smem_u32(bars + kXeStages + s));
+          mma_commit(smem_u32(bars + S + s));
         }
-        if (ok) mma_commit(smem_u32(bars + 2 * kXeStages + acc));
+        if (ok) mma_commit(smem_u32(bars + 2 * S + acc));
       }
       if (*abort_flag) {
-        const uint32_t drain = smem_u32(bars + 2 * kXeStages + 4);
+        // wait (bounded) for the MMAs already issued before TMEM is freed
+        const uint32_t drain = smem_u32(bars + 2 * S + 4);
         mma_commit(drain);
         for (int w = 0; w < (1 << 22) && !mbar_try(drain, 0); ++w) {
         }
       }
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;                        // TMEM lane quarter
+    const int half = (warp - 2) >> 2;              // which 128 outputs of the tile
     T* hh = static_cast<T*>(A.hh);
     int i = 0;
     for (long long u = blockIdx.x; u < tiles; u += gridDim.x, ++i) {
       const int acc = i & 1;
       const uint32_t aph = (i >> 1) & 1;
-      if (!mbar_wait(smem_u32(bars + 2 * kXeStages + acc), aph, abort_flag, A.err)) break;
+      if (!mbar_wait(smem_u32(bars + 2 * S + acc), aph, abort_flag, A.err)) break;
       tc_fence_after();
       const int mt = static_cast<int>(u / nt2), ot = static_cast<int>(u % nt2);
       const long long row = static_cast<long long>(mt) * kTile + q * 32 + lane;
@@ -861,25 +880,27 @@ __global__ void __launch_bounds__(kXeThreads, 1)
 #pragma unroll
       for (int ch = 0; ch < kTile / 32; ++ch) {
         float v[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32), v);
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                      static_cast<uint32_t>(acc * kRowN + half * kTile + ch * 32),
+                  v);
         if (live) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int kx = (ot * kTile + ch * 32) / 2 + j;
+            const int kx = (ot * kRowN + half * kTile + ch * 32) / 2 + j;
             store_lp(hh + ((static_cast<size_t>(c) * N + kx) * A.tb_cap + tl) * A.kp + 2 * jw, v[2 * j], v[2 * j + 1]);
           }
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(bars + 2 * kXeStages + 2 + acc));
+      if (lane == 0) mbar_arrive(smem_u32(bars + 2 * S + 2 + acc));
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kColTmemCols)
                  : "memory");
   }
 }
@@ -910,9 +931,9 @@ size_t tc_smem(int kp) { return tc_smem_bytes(kp); }
 
 cudaError_t tc_prepare(bool bf16, size_t smem) {
   cudaError_t e = bf16 ? cudaFuncSetAttribute(tc_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(xe_smem_bytes()))
+                                              static_cast<int>(tc_rows_smem_bytes()))
                        : cudaFuncSetAttribute(tc_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(xe_smem_bytes()));
+                                              static_cast<int>(tc_rows_smem_bytes()));
   if (e != cudaSuccess) return e;
   if (bf16)
     return cudaFuncSetAttribute(tc_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -944,7 +965,8 @@ bool tc_make_row_maps(void* gh, void* dftr, long long rows_cap, int n, int kr, b
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
   cuuint64_t df[2] = {static_cast<cuuint64_t>(kr), static_cast<cuuint64_t>(2 * n)};
-  return encode(static_cast<CUtensorMap*>(tm_fr), dt, 2, dftr, df, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  cuuint32_t box_fr[2] = {64, static_cast<cuuint32_t>(kRowN)};   // 256 outputs per tile
+  return encode(static_cast<CUtensorMap*>(tm_fr), dt, 2, dftr, df, strides, box_fr, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -961,12 +983,12 @@ cudaError_t launch_tc_batch(const TcArgs& a, const void* tm_dft, const void* tm_
   if (e != cudaSuccess) return e;
   {
     const long long rows = static_cast<long long>(nt) * a.u.n_chan * a.r_alloc;
-    const long long tiles = (rows + kTile - 1) / kTile * (2 * a.u.grid_n / kTile);
+    const long long tiles = (rows + kTile - 1) / kTile * (2 * a.u.grid_n / kRowN);
     const int grid = static_cast<int>(tiles < sms ? tiles : sms);
     const CUtensorMap* tg = static_cast<const CUtensorMap*>(a.tm_gh);
     const CUtensorMap* tf = static_cast<const CUtensorMap*>(a.tm_fr);
-    if (a.bf16) tc_rows_kernel<true><<<grid, kXeThreads, xe_smem_bytes(), s>>>(*tg, *tf, a, nt);
-    else tc_rows_kernel<false><<<grid, kXeThreads, xe_smem_bytes(), s>>>(*tg, *tf, a, nt);
+    if (a.bf16) tc_rows_kernel<true><<<grid, kTcThreads, tc_rows_smem_bytes(), s>>>(*tg, *tf, a, nt);
+    else tc_rows_kernel<false><<<grid, kTcThreads, tc_rows_smem_bytes(), s>>>(*tg, *tf, a, nt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
