@@ -81,7 +81,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("libepic build failed:\n" + msg)
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("libepic link failed:\n" + " ".join(link) + "\n" + r.stdout)

@@ -3,6 +3,7 @@
 #include "../../include/epic.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -17,6 +18,16 @@
 #include "epic_internal.h"
 
 namespace {
+
+// NVTX range over one entry point (named in timeline tools such as Nsight
+// Systems; a no-op without an attached tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 constexpr double kC = 299792458.0;  // speed of light, m/s
 constexpr double kPi = 3.14159265358979323846;
@@ -1000,6 +1011,7 @@ extern "C" {
 const char* epic_last_error(void) { return g_last_error.c_str(); }
 
 epic_status epic_plan_create(epic_plan_t* out, const epic_plan_desc* d) {
+  const NvtxRange nvtx_range("epic_plan_create");
   if (!out || !d) return fail(EPIC_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   epic::ImageKernelShape shape{};
@@ -1213,6 +1225,7 @@ epic_status epic_plan_get_info(epic_plan_t p, epic_plan_info* info) {
 }
 
 epic_status epic_set_gains(epic_plan_t p, const double* gains) {
+  const NvtxRange nvtx_range("epic_set_gains");
   if (epic_status s = check_plan(p)) return s;
   if (!gains) return fail(EPIC_ERR_INVALID_ARG, "gains is NULL");
   const size_t n = static_cast<size_t>(p->nc) * p->na;
@@ -1234,6 +1247,7 @@ epic_status epic_set_gains(epic_plan_t p, const double* gains) {
 
 epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
                        int accumulate) {
+  const NvtxRange nvtx_range("epic_image");
   if (epic_status s = check_plan(p)) return s;
   if (!d_volt || !d_image) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
@@ -1275,6 +1289,7 @@ epic_status epic_image(epic_plan_t p, const void* d_volt, long long n_time, doub
 
 epic_status epic_image_host(epic_plan_t p, const void* h_volt, long long n_time, double* h_image,
                             int accumulate) {
+  const NvtxRange nvtx_range("epic_image_host");
   if (epic_status s = check_plan(p)) return s;
   if (!h_volt || !h_image) return fail(EPIC_ERR_INVALID_ARG, "NULL host buffer");
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
@@ -1302,6 +1317,7 @@ epic_status epic_image_host(epic_plan_t p, const void* h_volt, long long n_time,
 
 epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_src,
                              const double* src, double gamma, const double* g0) {
+  const NvtxRange nvtx_range("epical_configure");
   if (epic_status s = check_plan(p)) return s;
   if (!(gamma >= 0.0 && gamma < 1.0)) return fail(EPIC_ERR_INVALID_ARG, "gamma must be in [0, 1)");
   if (n_src < 1 || !src) return fail(EPIC_ERR_INVALID_ARG, "at least one model source is required");
@@ -1366,6 +1382,7 @@ epic_status epical_configure(epic_plan_t p, double cal_l, double cal_m, int n_sr
 
 epic_status epic_visibilities(epic_plan_t p, const void* d_volt, long long n_time, double* d_vis,
                               int accumulate) {
+  const NvtxRange nvtx_range("epic_visibilities");
   if (epic_status s = check_plan(p)) return s;
   if (!d_volt || !d_vis) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
@@ -1421,6 +1438,7 @@ epic_status epic_visibilities(epic_plan_t p, const void* d_volt, long long n_tim
 
 epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_gains, int max_iter,
                                   double tol, double min_baseline, int* h_iters) {
+  const NvtxRange nvtx_range("epic_visibility_solve");
   if (epic_status s = check_plan(p)) return s;
   if (!p->cal || p->model.empty()) return fail(EPIC_ERR_STATE, "configure EPICal (the model) first");
   if (!d_vis || !d_gains || max_iter < 1 || !(tol >= 0.0) || !(min_baseline >= 0.0))
@@ -1483,6 +1501,7 @@ epic_status epic_visibility_solve(epic_plan_t p, const double* d_vis, double* d_
 }
 
 epic_status epical_configure_pixels(epic_plan_t p, int n_pix, const double* pix_lm) {
+  const NvtxRange nvtx_range("epical_configure_pixels");
   if (epic_status s = check_plan(p)) return s;
   if (!p->cal) return fail(EPIC_ERR_STATE, "configure EPICal (model, gamma) before its pixels");
   if (n_pix < 1 || !pix_lm) return fail(EPIC_ERR_INVALID_ARG, "need n_pix >= 1 and pix_lm");
@@ -1582,6 +1601,7 @@ epic_status epical_get_direction_gains(epic_plan_t p, double* h_gains) {
 }
 
 epic_status epical_average_channels(epic_plan_t p, int c_lo, int c_hi) {
+  const NvtxRange nvtx_range("epical_average_channels");
   if (epic_status s = check_plan(p)) return s;
   if (!(0 <= c_lo && c_lo < c_hi && c_hi <= p->nc))
     return fail(EPIC_ERR_INVALID_ARG, "channel band must satisfy 0 <= c_lo < c_hi <= C");
@@ -1627,6 +1647,7 @@ epic_status epic_set_phase_centre(epic_plan_t p, double l0, double m0) {
 }
 
 epic_status epical_fit_bandpass(epic_plan_t p, int c_lo, int c_hi, int deg_amp, int deg_phase) {
+  const NvtxRange nvtx_range("epical_fit_bandpass");
   if (epic_status s = check_plan(p)) return s;
   if (!(0 <= c_lo && c_lo < c_hi && c_hi <= p->nc))
     return fail(EPIC_ERR_INVALID_ARG, "channel band must satisfy 0 <= c_lo < c_hi <= C");
@@ -1652,6 +1673,7 @@ epic_status epical_fit_bandpass(epic_plan_t p, int c_lo, int c_hi, int deg_amp, 
 }
 
 epic_status epical_update(epic_plan_t p, double* d_gains_out, int* d_status) {
+  const NvtxRange nvtx_range("epical_update");
   if (epic_status s = check_plan(p)) return s;
   if (!p->cal) return fail(EPIC_ERR_STATE, "EPICal is not configured");
   if (p->frames < 1) return fail(EPIC_ERR_STATE, "no frames imaged since the last update");
@@ -1853,6 +1875,7 @@ epic_status time_image(epic_plan_t p, const void* d_volt, long long n_time, doub
 
 epic_status epic_autotune(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
                           epic_tune_result* out) {
+  const NvtxRange nvtx_range("epic_autotune");
   if (epic_status s = check_plan(p)) return s;
   if (!d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad autotune arguments");
   const bool cal = p->cal;
@@ -1951,6 +1974,7 @@ epic_status epic_autotune(epic_plan_t p, const void* d_volt, long long n_time, d
 
 epic_status epic_graph_capture(epic_plan_t p, const void* d_volt, long long n_time, double* d_image,
                                double* d_gains_out) {
+  const NvtxRange nvtx_range("epic_graph_capture");
   if (epic_status s = check_plan(p)) return s;
   if (!d_volt || !d_image || n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "bad capture arguments");
   if (!p->stream) return fail(EPIC_ERR_INVALID_ARG, "graph capture needs a non-default plan stream");
@@ -1999,6 +2023,7 @@ epic_status epic_graph_capture(epic_plan_t p, const void* d_volt, long long n_ti
 }
 
 epic_status epic_graph_launch(epic_plan_t p) {
+  const NvtxRange nvtx_range("epic_graph_launch");
   if (epic_status s = check_plan(p)) return s;
   if (!p->graph_exec) return fail(EPIC_ERR_STATE, "no captured graph");
   EPIC_CUDA(cudaGraphLaunch(p->graph_exec, p->stream));
@@ -2007,6 +2032,7 @@ epic_status epic_graph_launch(epic_plan_t p) {
 }
 
 epic_status epic_set_gains_device(epic_plan_t p, const double* d_gains) {
+  const NvtxRange nvtx_range("epic_set_gains_device");
   if (epic_status s = check_plan(p)) return s;
   if (!d_gains) return fail(EPIC_ERR_INVALID_ARG, "d_gains is NULL");
   EPIC_CUDA(epic::launch_set_gains(p->nc * p->na, reinterpret_cast<const double2*>(d_gains), p->d_gain.p,
@@ -2016,6 +2042,7 @@ epic_status epic_set_gains_device(epic_plan_t p, const double* d_gains) {
 
 epic_status epic_image_backward(epic_plan_t p, const void* d_volt, long long n_time,
                                 const double* d_dl_di, double* d_grad_g) {
+  const NvtxRange nvtx_range("epic_image_backward");
   if (epic_status s = check_plan(p)) return s;
   if (!d_volt || !d_dl_di || !d_grad_g) return fail(EPIC_ERR_INVALID_ARG, "NULL device buffer");
   if (n_time < 1) return fail(EPIC_ERR_INVALID_ARG, "n_time must be >= 1");
