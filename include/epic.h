@@ -360,12 +360,14 @@ epic_status epic_set_phase_centre(epic_plan_t plan, double l0, double m0);
 
 /* Failure detection (no counterpart in the paper): the warp-specialised
  * fused form (EPIC_PATH_PIPED) hands frames between its producer and
- * consumer warps through mbarriers, and every wait gives up after a bounded
- * number of polls; the kernel then raises the plan's error flag, stops
- * waiting and runs to its end, and the next epic_plan_sync returns
- * EPIC_ERR_TIMEOUT (the image of that call is not valid; the context stays
- * usable).  This call sets that number of polls for the plan's later
- * launches of that form (0 = the default, about 10^6); a small value makes
+ * consumer warps through mbarriers, and the persistent unfused form
+ * (batch_persistent) orders its phases with grid-wide barriers; every such
+ * wait gives up after a bounded number of polls, the kernel then raises the
+ * plan's error flag, stops waiting and runs to its end, and the next
+ * epic_plan_sync returns EPIC_ERR_TIMEOUT (the image of that call is not
+ * valid; the context stays usable).  This call sets that number of polls
+ * for the plan's later launches of those forms (0 = the default: about
+ * 10^6 for the mbarriers, 2^22 for the grid barrier); a small value makes
  * the waits run out, which is how the timeout path is tested.  Kernels that
  * have asynchronous copies in flight keep their own limits.  Host only.
  * Errors: INVALID_ARG (polls < 0). */

@@ -297,7 +297,8 @@ class Plan:
         B.check(self._lib.epic_set_phase_centre(self.handle, float(l0), float(m0)))
 
     def set_wait_limit(self, polls):
-        """Polls per bounded wait of the warp-specialised kernel (0 = default)."""
+        """Polls per bounded wait of the warp-specialised kernel and of the
+        persistent unfused kernel's grid barrier (0 = default)."""
         B.check(self._lib.epic_plan_set_wait_limit(self.handle, int(polls)))
 
     def update(self, gains_out=None, status=None):

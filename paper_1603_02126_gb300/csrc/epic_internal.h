@@ -270,6 +270,7 @@ struct UnfusedArgs {
   int row_table;           // row kernel's gather table: -1 auto, 0 L1, 1 shared memory
   int row_frames;          // row kernel's frames per step, 1 or 2
   int sms;                 // SMs of the device (persistent form's work split)
+  int wait_limit;          // persistent form: polls per grid-barrier wait (0 = default)
 };
 // One persistent cooperative launch for a whole call (N = 256, 512): rows,
 // grid barrier, columns, grid barrier, correlation, per batch of nt_batch

@@ -170,7 +170,7 @@ struct epic_plan_s {
   int tune_cols = 4;            // unfused: column units per SM to aim for
   int tune_row_table = -1;      // unfused row kernel: gather table -1 auto, 0 L1, 1 shared memory
   int tune_row_frames = 2;      // unfused row kernel: frames per step
-  int wait_limit = 0;           // warp-specialised form: polls per bounded wait (0 = default)
+  int wait_limit = 0;           // warp-specialised and persistent forms: polls per bounded wait (0 = default)
   int persistent = 0;           // unfused FP32, N = 256 / 512: one persistent launch per call
   int adjoint_precision = EPIC_PREC_FP32;   // arithmetic of the adjoint's transforms
   DevBuf<unsigned> d_gbar;      // grid barrier {count, generation, abort}
@@ -545,6 +545,7 @@ epic_status image_unfused(epic_plan_t p, const void* d_volt, long long n_time, d
   a.kacc = p->d_kacc.p;
   a.pacc = p->d_pacc.p;
   a.cols_target = p->tune_cols;
+  a.wait_limit = p->wait_limit;
   if (p->persistent && p->precision == EPIC_PREC_FP32 && epic::persistent_supported(N)) {
     a.row_frames = 1;
     EPIC_CUDA(epic::launch_unfused_persistent(a, n_time, static_cast<int>(nt), p->d_gbar.p, p->sms, p->stream));

@@ -481,8 +481,9 @@ dim3 correlate_grid(int n_chan, int n_ant, int nt, int sms) {
 // on the counter; the last arriver resets the counter and advances the
 // generation, the others wait for it with a bounded number of polls, after
 // which the kernel's abort flag and the plan's error flag are raised and
-// every CTA stops.  bar = {count, generation}.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+// every CTA stops.  bar = {count, generation, abort}; limit = polls per
+// wait (0: 2^22).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, int limit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -498,7 +499,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
         atomicAdd(bar + 1, 1u);
       } else {
         int i = 0;
-        for (; i < (1 << 22) && *vgen == g && *vabort == 0u; ++i) __nanosleep(64);
+        const int lim = limit > 0 ? limit : (1 << 22);
+        for (; i < lim && *vgen == g && *vabort == 0u; ++i) __nanosleep(64);
         if (*vgen == g) {
           ok = 0;
           atomicExch(bar + 2, 1u);
@@ -536,12 +538,12 @@ __global__ void __launch_bounds__(kUBT, (N <= 128 ? 3 : 2))
   for (long long t0 = 0; t0 < n_time; t0 += nt_batch) {
     const int nt = static_cast<int>(n_time - t0 < nt_batch ? n_time - t0 : nt_batch);
     rows_body<N, NZR, false>(A, t0, nt, tw, zbuf, rsm, blockIdx.x, gridDim.x);
-    if (!grid_barrier(bar, A.err)) return;
+    if (!grid_barrier(bar, A.err, A.wait_limit)) return;
     int segs = 1;
     while (C * CBLK * segs < A.cols_target * A.sms && segs * 8 <= nt) segs *= 2;
     cols_body<N, NZC, false, true>(A, nt, segs, tw, zbuf, nullptr, nullptr, &unused_abort, uses, blockIdx.x,
                                    gridDim.x);
-    if (!grid_barrier(bar, A.err)) return;
+    if (!grid_barrier(bar, A.err, A.wait_limit)) return;
     if (A.do_cal) {
       const int bx = (C * Na + 255) / 256;
       int sy = 1;

@@ -144,3 +144,34 @@ def test_persistent_launch_matches_oracle_and_batched(n, na, diam, C, T):
     # the replay images with the gains of the first update
     ref1, _ = O.image_interval(oplan, Eint, outs[0][1], block=4)
     assert _rel(img_g.cpu().numpy(), ref1) <= IMG_TOL
+
+
+def test_persistent_grid_barrier_timeout_is_reported_and_recoverable():
+    """Failure detection without a fault: with one poll per grid-barrier
+    wait the persistent kernel's early arrivers give up before the last CTA
+    arrives, raise the abort word and the plan's error flag, and every CTA
+    returns at its next barrier; epic_plan_sync reports EPIC_ERR_TIMEOUT.
+    With the default limit restored the same plan images correctly again."""
+    from paper_1603_02126_gb300 import EpicError, Plan
+    n, na, C, T = 256, 300, 2, 9
+    rng = np.random.default_rng(811)
+    ant = synth.layout_disc(na, 150.0, rng, 0.5)
+    freqs = np.linspace(45e6, 62e6, C)
+    sky = np.array([[0.0, 0.0, 5.0], [0.1, -0.2, 3.0]])
+    E = synth.voltages(ant, freqs, synth.true_gains(C, na, rng), sky, T, 1.0, rng)
+    lsb = np.full(C, 0.6)
+    b = synth.quantise_ci4(E, lsb)
+    d = torch.from_numpy(b).cuda()
+    kw = dict(support=3, param=0.5, input="ci4", voltage_scale=lsb, path="unfused",
+              workspace_bytes=3 * C * n * (n // 2 + 8) * 8)
+    p = Plan(ant, freqs, n, 0.5, batch_persistent=True, **kw)
+    p.set_wait_limit(1)
+    p.image(d)
+    with pytest.raises(EpicError) as ei:
+        p.sync()
+    assert ei.value.status == 6                       # EPIC_ERR_TIMEOUT
+    p.set_wait_limit(0)
+    img = p.image(d).cpu().numpy()
+    assert p.sync() == 0
+    ref = Plan(ant, freqs, n, 0.5, **kw).image(d).cpu().numpy()
+    assert _rel(img, ref) <= 1e-6
