@@ -230,6 +230,25 @@ def test_image_host_matches_device():
     assert _rel(h, d) < 1e-6     # same kernel; FP64 atomic order across segments differs
 
 
+def test_image_host_long_interval_matches_device_and_epical():
+    """The host-buffer call over a 2,100-sample interval: image and one
+    EPICal interval against the device call."""
+    w, b, Eint = _lwa_small(2, 2100)
+    pd, ph = _plan(w), _plan(w)
+    for p in (pd, ph):
+        p.configure((0.0, 0.0), w["model"], w["gamma"])
+    d = pd.image(torch.from_numpy(b).cuda()).cpu().numpy()
+    h = ph.image_host(b)
+    assert _rel(h, d) < 1e-6
+    gd = torch.zeros((2, 256), dtype=torch.complex128, device="cuda")
+    gh = torch.zeros((2, 256), dtype=torch.complex128, device="cuda")
+    pd.update(gd)
+    ph.update(gh)
+    assert pd.sync() == 0 and ph.sync() == 0
+    amp, phs = _gain_err(gh.cpu().numpy(), gd.cpu().numpy())
+    assert amp <= 1e-5 and phs <= 1e-5, (amp, phs)
+
+
 # --------------------------------------------------------------------------
 def test_epical_one_interval_matches_oracle():
     w, b, Eint = _lwa_small(2, 96)
