@@ -302,17 +302,19 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint_b2(const Adj
     const uint4* gcnt = A.gcnt + static_cast<size_t>(c) * A.rows_alloc * N1;
     const uint2* gent = A.gent + __ldg(A.gbase + c);
 
-    // R_k for this thread's pixels (column-FFT output order), as splat pairs
-    __nv_bfloat162 rk[G::NACC];
+    // R_k for this thread's pixels (column-FFT output order), two pixels
+    // per register as BF16 (splat when used)
+    __nv_bfloat162 rk[G::NACC / 2];
 #pragma unroll
     for (int r = 0; r < G::COLROUNDS; ++r) {
       const int kx = g + GROUPS * r;
 #pragma unroll
       for (int h = 0; h < H; ++h)
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
+        for (int k1 = 0; k1 < N1; k1 += 2) {
           const int ky = n1 + N1 * h + N2 * k1;
-          rk[r * N2 + h * N1 + k1] = __float2bfloat162_rn(static_cast<float>(__ldg(rimg + ky * N + kx)));
+          rk[(r * N2 + h * N1 + k1) / 2] = __floats2bfloat162_rn(static_cast<float>(__ldg(rimg + ky * N + kx)),
+                                                                 static_cast<float>(__ldg(rimg + (ky + N2) * N + kx)));
         }
     }
     // raw voltages (scaled) of the unit's first two frames and their E' = E / g
@@ -389,7 +391,8 @@ __global__ void __launch_bounds__(Cfg<N>::BT, 1) epic_image_adjoint_b2(const Adj
         for (int h = 0; h < H; ++h)
 #pragma unroll
           for (int k1 = 0; k1 < N1; ++k1) {
-            const __nv_bfloat162 rv = rk[r * N2 + h * N1 + k1];
+            const int ri = r * N2 + h * N1 + k1;
+            const __nv_bfloat162 rv = (ri & 1) ? __high2bfloat162(rk[ri >> 1]) : __low2bfloat162(rk[ri >> 1]);
             const Cb2 x = v[h * N1 + k1];
             w[h + H * k1] = Cb2{__hmul2(x.re, rv), __hneg2(__hmul2(x.im, rv))};
           }
