@@ -27,9 +27,9 @@
 // tcgen05.mma from one thread (M = 128 DFT rows, N = 256 = 128 frames of
 // two columns kx, kx + 1, K = 16 per instruction), warps 2-9 drain the
 // double-buffered TMEM accumulators (one warp per column and lane
-// quarter).  tc_rows (N = 256 outputs per MMA, epilogue warps 2-9) and the
-// X-engine (epilogue warps 2-5) stream both operands through a 4-stage
-// ring.
+// quarter).  tc_rows (N = 256 outputs per MMA) and the X-engine (N = 256
+// columns per MMA) stream both operands through a 4-stage ring, with
+// epilogue warps 2-9.
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, waits (bounded) for its copies and MMAs in flight and winds down.
 #include <cuda.h>
@@ -307,8 +307,7 @@ constexpr int kChunkBytes = kTile * 128; // one 64-element K chunk of a 128-row 
 constexpr int kColN = 256;               // MMA N of tc_cols: 128 frames of kx, then of kx + 1
 constexpr int kColChunkBytes = kColN * 128;
 constexpr int kColStages = 4;            // K-chunk ring of the data operand
-constexpr uint32_t kTmemCols = 256;      // tc_rows / X-engine: two 128-column accumulators
-constexpr uint32_t kColTmemCols = 512;   // tc_cols: two 256-column accumulators
+constexpr uint32_t kColTmemCols = 512;   // tc_cols, tc_rows, X-engine: two 256-column accumulators
 
 // Dynamic shared memory of tc_cols_kernel for a K extent of kp elements:
 // the CTA's resident DFT tile and the data ring.
@@ -515,15 +514,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Per channel the voltages become a real matrix Z [2 Na_p][Tp] of FP16
 // integers (row 2a = Re E_a, row 2a + 1 = Im E_a, time contiguous, zero
 // padded); G = Z Z^T by tcgen05.mma (M = N = 128, K = 16 per instruction,
-// FP32 accumulation in TMEM), upper-triangle 128 x 128 tiles only.  The
+// FP32 accumulation in TMEM), tiles of 128 rows by 256 columns (two column
+// blocks, M = 128, N = 256 per MMA) on or above the diagonal; the block of
+// a tile that falls below the diagonal is computed but not written.  The
 // 4-bit values and every partial sum are integers below 2^24, so G is
 // exact.  Epilogue: Re V_ab = G[2a][2b] + G[2a+1][2b+1],
 // Im V_ab = G[2a+1][2b] - G[2a][2b+1] (rows 2a and 2a+1 are adjacent TMEM
 // lanes, exchanged by one shuffle), times s_c^2 / T in FP64.
 // ---------------------------------------------------------------------------
 constexpr int kXeStages = 4;                 // K-chunk ring (A and B chunk per stage)
-constexpr int kXeThreads = 192;              // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-constexpr uint32_t kXeStageBytes = 2 * kChunkBytes;
+constexpr int kXeThreads = 320;              // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kXeN = 256;                    // columns per tile: two 128-row blocks of Z
+constexpr uint32_t kXeStageBytes = kChunkBytes + kXeN * 128;
 
 size_t xe_smem_bytes() { return 1024 + kXeStages * kXeStageBytes + 256; }
 
@@ -568,7 +570,9 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kXeStages + 6);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = 2 * A.na_p / kTile;                        // row blocks per channel
-  const int pairs = nb * (nb + 1) / 2;
+  const int nbp = (nb + 1) / 2;                             // column block pairs
+  int pairs = 0;                                            // tiles per channel
+  for (int i = 0; i < nb; ++i) pairs += nbp - i / 2;
   const long long tiles = static_cast<long long>(A.n_chan) * pairs;
   const int kc_n = A.tp / 64;
 
@@ -579,7 +583,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(bars + 2 * kXeStages + i), 1);
-      mbar_init(smem_u32(bars + 2 * kXeStages + 2 + i), 4);
+      mbar_init(smem_u32(bars + 2 * kXeStages + 2 + i), 8);
     }
     mbar_init(smem_u32(bars + 2 * kXeStages + 4), 1);
     *abort_flag = 0;
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(kColTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -596,17 +600,18 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  // tile u -> (channel, row block bi, column block bj), bi <= bj
-  auto tile_of = [&](long long u, int* c, int* bi, int* bj) {
+  // tile u -> (channel, row block bi, column blocks 2 bjp and 2 bjp + 1),
+  // bjp >= bi / 2 (the pair reaches the diagonal)
+  auto tile_of = [&](long long u, int* c, int* bi, int* bjp) {
     *c = static_cast<int>(u / pairs);
     int pr = static_cast<int>(u - static_cast<long long>(*c) * pairs);
     int i = 0;
-    while (pr >= nb - i) {
-      pr -= nb - i;
+    while (pr >= nbp - i / 2) {
+      pr -= nbp - i / 2;
       ++i;
     }
     *bi = i;
-    *bj = i + pr;
+    *bjp = i / 2 + pr;
   };
 
   if (warp == 0) {
@@ -614,9 +619,9 @@ __global__ void __launch_bounds__(kXeThreads, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_z)) : "memory");
       long long it = 0;                                       // K chunks issued so far
       for (long long u = blockIdx.x; u < tiles && !*abort_flag; u += gridDim.x) {
-        int c, bi, bj;
-        tile_of(u, &c, &bi, &bj);
-        const int ya = c * 2 * A.na_p + bi * kTile, yb = c * 2 * A.na_p + bj * kTile;
+        int c, bi, bjp;
+        tile_of(u, &c, &bi, &bjp);
+        const int ya = c * 2 * A.na_p + bi * kTile, yb = c * 2 * A.na_p + 2 * bjp * kTile;
         for (int kc = 0; kc < kc_n; ++kc, ++it) {
           const int s = static_cast<int>(it % kXeStages);
           const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
@@ -626,6 +631,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
           unsigned char* st = base + s * kXeStageBytes;
           tma_load_2d(smem_u32(st), &tm_z, kc * 64, ya, bfull);
           tma_load_2d(smem_u32(st + kChunkBytes), &tm_z, kc * 64, yb, bfull);
+          tma_load_2d(smem_u32(st + 2 * kChunkBytes), &tm_z, kc * 64, yb + kTile, bfull);
         }
       }
       if (*abort_flag) {
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(kTile >> 3) << 17) |
+      const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(kXeN >> 3) << 17) |
                              (static_cast<uint32_t>(kTile >> 4) << 24);   // FP16 x FP16 -> FP32
       long long it = 0;
       int i = 0;
@@ -649,7 +655,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
         const uint32_t aph = (i >> 1) & 1;
         if (!mbar_wait(smem_u32(bars + 2 * kXeStages + 2 + acc), aph ^ 1, abort_flag, A.err)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kTile);
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * kXeN);
         for (int kc = 0; kc < kc_n; ++kc, ++it) {
           const int s = static_cast<int>(it % kXeStages);
           const uint32_t ph = static_cast<uint32_t>((it / kXeStages) & 1);
@@ -675,8 +681,10 @@ __global__ void __launch_bounds__(kXeThreads, 1)
       }
     }
   } else {
-    // epilogue: warp (2..5) & 3 is the TMEM lane quarter it may read
+    // epilogue: warp (2..9) & 3 is the TMEM lane quarter it may read, and
+    // (warp - 2) / 4 the column block of the pair it writes
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = q * 32 + lane;                             // tile row 2a' + s
     int i = 0;
     for (long long u = blockIdx.x; u < tiles; u += gridDim.x, ++i) {
@@ -684,8 +692,10 @@ __global__ void __launch_bounds__(kXeThreads, 1)
       const uint32_t aph = (i >> 1) & 1;
       if (!mbar_wait(smem_u32(bars + 2 * kXeStages + acc), aph, abort_flag, A.err)) break;
       tc_fence_after();
-      int c, bi, bj;
-      tile_of(u, &c, &bi, &bj);
+      int c, bi, bjp;
+      tile_of(u, &c, &bi, &bjp);
+      const int bj = 2 * bjp + half;
+      const bool upper = bj >= bi;                           // else the block lies below the diagonal
       const int a = (bi * kTile + r) >> 1;                   // antenna of this lane pair
       const bool even = (lane & 1) == 0;
       const float vs = A.vscale ? __ldg(A.vscale + c) : 1.0f;
@@ -694,13 +704,15 @@ __global__ void __launch_bounds__(kXeThreads, 1)
 #pragma unroll
       for (int ch = 0; ch < kTile / 32; ++ch) {
         float v[32];
-        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * kTile + ch * 32), v);
+        tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                      static_cast<uint32_t>(acc * kXeN + half * kTile + ch * 32),
+                  v);
         // v[2j + s'] = G[r][bj*128 + ch*32 + 2j + s']; partner lane holds row r ^ 1
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float p0 = __shfl_xor_sync(fft::kFull, v[2 * j], 1);
           const float p1 = __shfl_xor_sync(fft::kFull, v[2 * j + 1], 1);
-          if (even) {
+          if (even && upper) {
             const int b = (bj * kTile + ch * 32 + 2 * j) >> 1;
             if (a < A.n_ant && b < A.n_ant) {
               // row 2a: v = G[2a][2b], G[2a][2b+1]; partner: G[2a+1][2b], G[2a+1][2b+1]
@@ -727,7 +739,7 @@ __global__ void __launch_bounds__(kXeThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kColTmemCols)
                  : "memory");
   }
 }
@@ -1037,8 +1049,10 @@ cudaError_t launch_xengine_tc(const XeTcArgs& a, const void* volt, long long t0,
                                     a.tp, static_cast<__half*>(z));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nb = 2 * a.na_p / kTile;
-  const long long tiles = static_cast<long long>(a.n_chan) * nb * (nb + 1) / 2;
+  const int nb = 2 * a.na_p / kTile, nbp = (nb + 1) / 2;
+  long long pairs = 0;
+  for (int i = 0; i < nb; ++i) pairs += nbp - i / 2;
+  const long long tiles = static_cast<long long>(a.n_chan) * pairs;
   const int grid = static_cast<int>(tiles < sms ? tiles : sms);
   xengine_tc_kernel<<<grid, kXeThreads, xe_smem_bytes(), s>>>(*static_cast<const CUtensorMap*>(tm), a);
   return cudaGetLastError();
